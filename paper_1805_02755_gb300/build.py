@@ -1,0 +1,81 @@
+"""Builds libecl.so in-tree with nvcc for sm_103a (no torch extension machinery).
+
+Each .cu file is compiled to an object in parallel, then the objects are
+linked into one shared library next to this file.  The Mandelbrot unit is
+compiled with -fmad=false (its counts must match a correctly rounded host
+evaluation bit for bit).
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libecl.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+# source -> extra flags
+SOURCES = {
+    "runtime.cu": [],
+    "registry.cu": [],
+    "k_mandelbrot.cu": ["-fmad=false"],
+}
+HEADERS = ["ecl_internal.h", "sched.cuh"]
+
+
+def nvcc() -> str:
+    for c in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found")
+
+
+def _stale(obj: str, deps) -> bool:
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(verbose: bool = False, force: bool = False, jobs: int = 8) -> str:
+    os.makedirs(OBJ, exist_ok=True)
+    cc = nvcc()
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "ecl.h"), __file__]
+    common = [cc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-I", inc, "--expt-relaxed-constexpr"]
+    cmds = []
+    objs = []
+    for src, extra in SOURCES.items():
+        s = os.path.join(CSRC, src)
+        o = os.path.join(OBJ, src.replace(".cu", ".o"))
+        objs.append(o)
+        if force or _stale(o, [s] + hdrs):
+            cmds.append(common + extra + ["-c", s, "-o", o])
+
+    def run(cmd):
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
+        if verbose and (r.stdout or r.stderr):
+            print(r.stdout + r.stderr, flush=True)
+
+    if cmds:
+        with ThreadPoolExecutor(max_workers=jobs) as ex:
+            list(ex.map(run, cmds))
+    if force or cmds or not os.path.exists(LIB) or _stale(LIB, objs):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        run([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))

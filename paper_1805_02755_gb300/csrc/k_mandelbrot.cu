@@ -1,0 +1,185 @@
+// Mandelbrot escape counts (Sec. 5.3 Fig. 6 workload; Table 2: lws 256, no
+// input buffer, out pattern 4:1).  This translation unit is compiled with
+// -fmad=false and every operation is written with an explicit round-to-
+// nearest intrinsic, so the FP32 arithmetic is exactly the correctly
+// rounded sequence of the definition and the counts match a host
+// evaluation bit for bit.
+//
+// Work-item g computes pixels 4g .. 4g+3 of the row-major image and writes
+// them with one 128-bit store.  One chunk = one work-group; the CTA (256
+// threads) strides over the work-group's work-items.  The four pixels of a
+// thread iterate interleaved so that four independent dependency chains
+// are in flight.
+#include <cuda_runtime.h>
+
+#include "ecl_internal.h"
+#include "sched.cuh"
+
+namespace ecl {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct MandelbrotBody {
+    struct Params {
+        uint32_t *out;
+        int64_t W, H;
+        float x0, y0, dx, dy;
+        int32_t max_iter;
+        uint32_t lws;
+    };
+    Params p;
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
+    {
+        return (uint32_t)len;
+    }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const uint64_t npx = (uint64_t)p.W * (uint64_t)p.H;
+        const uint64_t wg = off + t;
+        const uint64_t wi_end = (wg + 1) * p.lws;
+        for (uint64_t wi = wg * p.lws + threadIdx.x; wi < wi_end; wi += blockDim.x) {
+            const uint64_t px0 = wi * 4;
+            if (px0 >= npx) break;
+            float cx[4], cy[4], x[4], y[4];
+            uint32_t n[4];
+            bool live[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t px = px0 + k;
+                const uint64_t i = px % (uint64_t)p.W, j = px / (uint64_t)p.W;
+                cx[k] = __fadd_rn(p.x0, __fmul_rn((float)i, p.dx));
+                cy[k] = __fadd_rn(p.y0, __fmul_rn((float)j, p.dy));
+                x[k] = 0.0f;
+                y[k] = 0.0f;
+                n[k] = 0;
+                live[k] = px < npx;
+            }
+            for (int32_t it = 0; it < p.max_iter; ++it) {
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float x2 = __fmul_rn(x[k], x[k]);
+                    const float y2 = __fmul_rn(y[k], y[k]);
+                    const bool go = live[k] && !(__fadd_rn(x2, y2) > 4.0f);
+                    const float xt = __fadd_rn(__fsub_rn(x2, y2), cx[k]);
+                    const float yt = __fadd_rn(__fmul_rn(__fmul_rn(2.0f, x[k]), y[k]), cy[k]);
+                    x[k] = go ? xt : x[k];
+                    y[k] = go ? yt : y[k];
+                    n[k] += go ? 1u : 0u;
+                    live[k] = go;
+                    any |= go;
+                }
+                if (!any) break;
+            }
+            if (px0 + 3 < npx) {
+                *reinterpret_cast<uint4 *>(p.out + px0) = make_uint4(n[0], n[1], n[2], n[3]);
+            } else {
+                for (int k = 0; k < 4; ++k)
+                    if (px0 + k < npx) p.out[px0 + k] = n[k];
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kBlock) k_mandelbrot(MandelbrotBody::Params prm, SchedArgs s)
+{
+    MandelbrotBody b{prm};
+    drive(s, b);
+}
+
+MandelbrotBody::Params params_of(const KArgs &a, uint32_t lws)
+{
+    MandelbrotBody::Params p;
+    p.out = a.buf<uint32_t>(0);
+    p.W = a.i32(1);
+    p.H = a.i32(2);
+    p.x0 = a.f32(3);
+    p.y0 = a.f32(4);
+    p.dx = a.f32(5);
+    p.dy = a.f32(6);
+    p.max_iter = a.i32(7);
+    p.lws = lws;
+    return p;
+}
+
+ecl_status validate(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    const int64_t W = a.i32(1), H = a.i32(2);
+    if (W <= 0 || H <= 0) {
+        err = "width and height must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (a.i32(7) < 0) {
+        err = "max_iter must be >= 0";
+        return ECL_ERR_ARG;
+    }
+    if (lws > 1024) {
+        err = "lws must be <= 1024";
+        return ECL_ERR_SIZE;
+    }
+    const uint64_t npx = (uint64_t)W * (uint64_t)H;
+    if (a.bytes[0] < npx * 4) {
+        err = "output buffer smaller than width*height uint32";
+        return ECL_ERR_BUFFER;
+    }
+    if ((uintptr_t)a.ptr[0] % 16) {
+        err = "output buffer must be 16-byte aligned";
+        return ECL_ERR_BUFFER;
+    }
+    if (gws * 4 < npx) {
+        err = "the NDRange (4 pixels per work-item) does not cover the image";
+        return ECL_ERR_SIZE;
+    }
+    return ECL_OK;
+}
+
+uint64_t grain(const KArgs &, uint64_t, uint32_t) { return 1; }
+
+uint32_t nchunks(const KArgs &a, uint64_t, uint32_t lws, uint64_t off, uint64_t len)
+{
+    return MandelbrotBody::nchunks(params_of(a, lws), off, len);
+}
+
+int ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mandelbrot, kBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    k_mandelbrot<<<c.grid, kBlock, 0, c.stream>>>(params_of(a, c.lws), s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
+}
+
+}  // namespace
+
+extern const KernelDesc kMandelbrot = {
+    "mandelbrot",
+    8,
+    {{"out", A_BUF_OUT}, {"width", A_I32}, {"height", A_I32}, {"x0", A_F32}, {"y0", A_F32},
+     {"dx", A_F32}, {"dy", A_F32}, {"max_iter", A_I32}},
+    4,
+    1,
+    kBlock,
+    0,
+    validate,
+    grain,
+    nchunks,
+    ctas_per_sm,
+    launch,
+};
+
+}  // namespace ecl

@@ -1,0 +1,40 @@
+// Name -> kernel table of the built-in kernels, and the argument
+// introspection call the Python binding uses to marshal values.
+#include <string.h>
+
+#include "ecl_internal.h"
+
+namespace ecl {
+
+extern const KernelDesc kMandelbrot;
+
+static const KernelDesc *const kAll[] = {
+    &kMandelbrot,
+};
+
+const KernelDesc *find_kernel(const char *name)
+{
+    for (const KernelDesc *k : kAll)
+        if (strcmp(k->name, name) == 0) return k;
+    return nullptr;
+}
+
+}  // namespace ecl
+
+extern "C" ecl_status ecl_kernel_arg(const char *kernel_name, int index, int *kind, const char **name)
+{
+    const ecl::KernelDesc *k = kernel_name ? ecl::find_kernel(kernel_name) : nullptr;
+    if (!k) return ECL_ERR_KERNEL;
+    if (index < 0 || index >= k->nargs) return ECL_ERR_ARG;
+    if (kind) *kind = (int)k->args[index].kind;
+    if (name) *name = k->args[index].name;
+    return ECL_OK;
+}
+
+extern "C" int ecl_kernel_count(void) { return (int)(sizeof(ecl::kAll) / sizeof(ecl::kAll[0])); }
+
+extern "C" const char *ecl_kernel_name(int i)
+{
+    if (i < 0 || i >= ecl_kernel_count()) return nullptr;
+    return ecl::kAll[i]->name;
+}

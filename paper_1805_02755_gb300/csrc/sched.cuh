@@ -1,0 +1,263 @@
+// Device side of the package scheduler: the persistent-CTA driver that every
+// kernel body runs under.
+//
+// The paper's devices (Sec. 5.1: one host thread per OpenCL device, the
+// Scheduler thread handing out packages) become groups of C persistent CTAs.
+// A package taken by a device is split into chunks; the device's CTAs claim
+// chunks through one 64-bit word per device.  The CTA whose claim lands
+// exactly one past the last chunk is the one that fetches the device's next
+// package (Static: its own range once; Dynamic/HGuided: the next entry of
+// the queue).  Other CTAs of the device that overshoot wait, with a bounded
+// spin, for the new package to be published.  Nothing else waits, so the
+// queue cannot deadlock: the CTA being waited for is running.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ecl_internal.h"
+
+namespace ecl {
+
+__device__ __forceinline__ uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smid()
+{
+    uint32_t s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+struct Claim {
+    uint64_t off, len;   // package range (work-groups)
+    uint32_t pkg;        // package index
+    uint32_t t_begin;    // chunks [t_begin, t_end) of nchunks
+    uint32_t t_end;
+    uint32_t nchunks;
+    uint32_t done;       // no more work for this CTA
+    uint32_t last;       // (exit) this CTA is the last to leave
+};
+
+// HGuided packet size of device d for G_r pending units (Sec. 5.3 equation),
+// evaluated in double in the order (G_r * P_i) / ((k * n) * sum P), raised
+// to the device minimum and clipped to G_r.
+__device__ __forceinline__ uint64_t hguided_units(const SchedArgs &s, uint32_t d, uint64_t gr)
+{
+    const double q = ((double)gr * s.hg_p[d]) / ((s.hg_k * (double)s.D) * s.hg_sum_p);
+    uint64_t sz = (uint64_t)floor(q);
+    const uint64_t mn = s.hg_min[d];
+    if (sz < mn) sz = mn;
+    if (sz > gr) sz = gr;
+    return sz;
+}
+
+// Takes the next package for device d; returns its slot or -1 when none is
+// left.  Called by one thread of one CTA of the device at a time.
+template <class Body>
+__device__ int64_t fetch_package(const SchedArgs &s, const typename Body::Params &bp, uint32_t d)
+{
+    int64_t p = -1;
+    if (s.mode == MODE_STATIC) {
+        if (atomicAdd(&s.dev[d].fetches, 1u) == 0u) p = d;
+    } else if (s.mode == MODE_QUEUE) {
+        const unsigned long long i = atomicAdd(&s.q->cursor, 1ull);
+        if (i < s.npkg) p = (int64_t)i;
+    } else {  // MODE_HGUIDED: cut the package from the pending units
+        unsigned long long used = ld_relaxed(&s.q->consumed);
+        while (used < s.units) {
+            const uint64_t gr = s.units - used;
+            const uint64_t sz = hguided_units(s, d, gr);
+            const unsigned long long seen = atomicCAS(&s.q->consumed, used, used + sz);
+            if (seen == used) {
+                const uint64_t off = used * s.grain;
+                uint64_t end = (used + sz) * s.grain;
+                if (end > s.G) end = s.G;
+                const unsigned long long i = atomicAdd(&s.q->cursor, 1ull);
+                if (i >= s.table_cap) break;  // cannot happen: every package has >= 1 unit
+                Pkg pk;
+                pk.off = off;
+                pk.len = end - off;
+                pk.nchunks = Body::nchunks(bp, off, end - off);
+                pk.pad = 0;
+                s.table[i] = pk;
+                p = (int64_t)i;
+                break;
+            }
+            used = seen;
+        }
+    }
+    if (p >= 0) {
+        const Pkg pk = s.table[p];
+        PkgRec r;
+        r.off = pk.off;
+        r.len = pk.len;
+        r.t0 = gtime();
+        r.t1 = 0;
+        r.pkg = (uint32_t)p;
+        r.device = d;
+        r.cta = blockIdx.x;
+        r.smid = smid();
+        r.done = 0;
+        r.nchunks = pk.nchunks;
+        s.rec[p] = r;
+        __threadfence();
+    }
+    return p;
+}
+
+template <class Body>
+__device__ Claim claim_chunks(const SchedArgs &s, const typename Body::Params &bp, uint32_t d)
+{
+    Claim c{};
+    if (s.C == 1) {
+        const int64_t p = fetch_package<Body>(s, bp, d);
+        if (p < 0) {
+            c.done = 1;
+            return c;
+        }
+        const Pkg pk = s.table[p];
+        c.off = pk.off;
+        c.len = pk.len;
+        c.pkg = (uint32_t)p;
+        c.t_begin = 0;
+        c.t_end = pk.nchunks;
+        c.nchunks = pk.nchunks;
+        return c;
+    }
+    uint32_t spins = 0;
+    for (;;) {
+        const unsigned long long w = atomicAdd(&s.dev[d].word, 1ull);
+        const uint32_t slot = (uint32_t)(w >> 32);
+        const uint32_t t = (uint32_t)w;
+        if (slot == kSlotDone) {
+            c.done = 1;
+            return c;
+        }
+        __threadfence();
+        const uint32_t nch = slot ? s.table[slot - 1].nchunks : 0u;
+        if (t < nch) {
+            const Pkg pk = s.table[slot - 1];
+            c.off = pk.off;
+            c.len = pk.len;
+            c.pkg = slot - 1;
+            c.t_begin = t;
+            c.t_end = t + 1;
+            c.nchunks = nch;
+            return c;
+        }
+        if (t == nch) {  // this CTA fetches the device's next package
+            const int64_t p = fetch_package<Body>(s, bp, d);
+            if (p < 0) {
+                atomicExch(&s.dev[d].word, (unsigned long long)kSlotDone << 32);
+                c.done = 1;
+                return c;
+            }
+            atomicExch(&s.dev[d].word, (unsigned long long)(p + 1) << 32);
+            continue;
+        }
+        // another CTA of the device is fetching: wait for the new slot
+        while ((uint32_t)(ld_relaxed(&s.dev[d].word) >> 32) == slot) {
+            __nanosleep(128);
+            if (++spins > s.spin_limit) {
+                atomicExch(&s.q->error, (unsigned int)ECL_ERR_TIMEOUT);
+                atomicExch(&s.q->error_info, ((unsigned long long)blockIdx.x << 32) | spins);
+                c.done = 1;
+                return c;
+            }
+        }
+    }
+}
+
+// The persistent driver.  Body must provide
+//   struct Params;                                   (kernel arguments)
+//   static __host__ __device__ uint32_t nchunks(const Params&, off, len);
+//   __device__ void run(off, len, t, nchunks);        (all threads, uniform)
+template <class Body>
+__device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
+{
+    __shared__ Claim sc;
+    if (s.mode == MODE_MONO) {  // the whole range is one package, CTA b = chunk b
+        body.run(0, s.G, blockIdx.x, s.mono_nchunks);
+        return;
+    }
+    const uint32_t d = blockIdx.x / s.C;
+    uint64_t t_first = 0, t_last = 0, busy = 0;
+    uint32_t nchunks_done = 0;
+    for (;;) {
+        if (threadIdx.x == 0) sc = claim_chunks<Body>(s, body.p, d);
+        __syncthreads();
+        const Claim c = sc;
+        __syncthreads();
+        if (c.done) break;
+        uint64_t ts = 0;
+        if (threadIdx.x == 0) ts = gtime();
+        for (uint32_t t = c.t_begin; t < c.t_end; ++t) body.run(c.off, c.len, t, c.nchunks);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint64_t te = gtime();
+            if (!t_first) t_first = ts;
+            t_last = te;
+            busy += te - ts;
+            nchunks_done += c.t_end - c.t_begin;
+            const uint32_t n = c.t_end - c.t_begin;
+            const uint32_t prev = (s.C == 1) ? 0u : atomicAdd(&s.rec[c.pkg].done, n);
+            const bool pkg_finished = (prev + n == c.nchunks);
+            if (pkg_finished) {
+                s.rec[c.pkg].t1 = te;
+                s.rec[c.pkg].done = c.nchunks;
+            }
+            sc.last = pkg_finished ? 1u : 0u;
+        }
+        if (s.coverage) {  // debug: count every work-group of a finished package
+            __syncthreads();
+            if (sc.last)
+                for (uint64_t w = c.off + threadIdx.x; w < c.off + c.len; w += blockDim.x)
+                    atomicAdd(&s.coverage[w], 1u);
+            __syncthreads();
+        }
+    }
+    // exit: per-CTA record, then the last CTA out resets the queue
+    if (threadIdx.x == 0) {
+        ecl_worker_stat w;
+        w.t_first_ns = t_first;
+        w.t_last_ns = t_last;
+        w.busy_ns = busy;
+        w.cta = blockIdx.x;
+        w.device = d;
+        w.smid = smid();
+        w.chunks = nchunks_done;
+        s.wst[blockIdx.x] = w;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&s.q->exit_count, 1u);
+        sc.last = (ticket == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (sc.last) {
+        __threadfence();
+        for (uint32_t i = threadIdx.x; i < s.D; i += blockDim.x) {
+            s.dev[i].word = 0ull;
+            s.dev[i].fetches = 0u;
+        }
+        if (threadIdx.x == 0) {
+            s.q->last_npkg = s.q->cursor;
+            s.q->cursor = 0ull;
+            s.q->consumed = 0ull;
+            s.q->exit_count = 0u;
+        }
+        __threadfence();
+    }
+}
+
+}  // namespace ecl

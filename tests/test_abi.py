@@ -1,0 +1,88 @@
+"""The C ABI library builds, loads and exports every symbol include/ecl.h declares.
+
+Only host-side calls run here (no GPU): program creation, argument checks and
+the package planner.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+KERNELS = ["mandelbrot"]
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_1805_02755_gb300 import build as B
+    B.build()
+    import paper_1805_02755_gb300 as E
+    return E
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ecl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ecl_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["ecl_engine_create", "ecl_engine_destroy", "ecl_program_create", "ecl_program_in",
+              "ecl_program_out", "ecl_program_out_pattern", "ecl_program_arg", "ecl_program_local",
+              "ecl_engine_program", "ecl_work_items", "ecl_scheduler", "ecl_workers", "ecl_run",
+              "ecl_stats", "ecl_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(E):
+    L = ctypes.CDLL(E.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_uses_the_same_names(E):
+    for n in declared_functions():
+        assert hasattr(E, n), n
+
+
+def test_builtin_kernels(E):
+    assert E.ecl_kernel_names() == KERNELS
+    # Table 2: Mandelbrot takes 8 arguments
+    kinds = []
+    i = 0
+    while E.ecl_kernel_arg("mandelbrot", i) is not None:
+        kinds.append(E.ecl_kernel_arg("mandelbrot", i))
+        i += 1
+    assert len(kinds) == 8 and kinds[0] == (E.ECL_ARG_BUF_OUT, "out")
+
+
+def test_program_errors_without_gpu(E):
+    with pytest.raises(E.EclError) as ei:
+        E.ecl_program_create("no_such_kernel")
+    assert ei.value.status == E.ECL_ERR_KERNEL
+    p = E.ecl_program_create("mandelbrot")
+    try:
+        L = E.lib()
+        v = ctypes.c_int32(5)
+        assert L.ecl_program_arg(p, 8, ctypes.byref(v), 4) == E.ECL_ERR_ARG      # past the last arg
+        assert L.ecl_program_arg(p, 1, ctypes.byref(v), 8) == E.ECL_ERR_ARG      # wrong size
+        assert L.ecl_program_arg(p, 1, ctypes.byref(v), 4) == E.ECL_OK
+        assert L.ecl_program_arg(p, -1, ctypes.byref(v), 4) == E.ECL_OK          # aggregate: index 2
+        assert L.ecl_program_local(p, 3, 1024) == E.ECL_ERR_ARG                  # no local args
+        assert L.ecl_program_out_pattern(p, 0, 1) == E.ECL_ERR_ARG
+        assert L.ecl_program_in(p, None, 16) == E.ECL_ERR_ARG
+    finally:
+        E.ecl_program_destroy(p)
+
+
+def test_null_handles(E):
+    L = E.lib()
+    assert L.ecl_run(None) == E.ECL_ERR_ARG
+    assert L.ecl_work_items(None, 1, 1) == E.ECL_ERR_ARG
+    assert L.ecl_synchronize(None) == E.ECL_ERR_ARG
+    assert L.ecl_engine_create(None, 0, None) == E.ECL_ERR_ARG
+    L.ecl_engine_destroy(None)
+    assert L.ecl_last_error(None) == b"NULL engine"
