@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: one step = one run of every configured program.
+
+Configurations (seeded synthetic inputs, see workloads.py):
+  mandelbrot  1024x1024, [-2,1]x[-1.5,1.5], 256 iterations, Static, one package
+  gaussian    8192x8192 FP32, 31 taps sigma 5, clamp, Dynamic 256 row packages
+
+Each program is one ecl_run() through the C ABI (one persistent launch).  The
+JSON line reports:
+  value        work-items per second over the whole step (device-timed, inputs
+               resident in HBM, L2 flushed before every step)
+  e2e          the same through the public API with pinned HOST buffers: the
+               engine copies inputs in and outputs out inside the timed region
+  roofline     the dominant kernel against its bound
+  kernels      per program: time, work-items/s, own-unit rate, roofline
+               fraction, scheduler overhead against a monolithic launch
+               (Sec. 7.3 overhead metric) and the load balance T_FD/T_LD
+  cpu_baseline the CPU oracle on a bounded sample of the same step
+--impl reference times the CPU oracle on this config (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
+L2_FLUSH_BYTES = 512 << 20
+SMS_NOMINAL = 152
+SM_MAX_MHZ = 2070.0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=d.get("hbm_gbs", 6800.0), bf16_tflops=d.get("bf16_tflops", 1900.0),
+                    bf16_tflops_sustained=d.get("bf16_tflops_sustained", 1700.0),
+                    sm_max_mhz=d.get("sm_max_mhz", SM_MAX_MHZ), src="measured")
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=SM_MAX_MHZ,
+                src="fallback")
+
+
+def fp32_peak_tflops(sms, mhz):
+    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA, at the given SM clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ====================================================================== workloads
+class Workload:
+    name = ""
+    sched = ()
+    host_ok = True
+
+    def __init__(self, E, torch, dev):
+        self.E, self.torch, self.dev = E, torch, dev
+
+    # builds self.eng (device buffers) and self.mono (monolithic launch)
+    def setup(self):
+        raise NotImplementedError
+
+    def programs(self, inputs, outputs):
+        raise NotImplementedError
+
+    def make_engine(self, sched, params, D=0, C=0, host=False):
+        E = self.E
+        eng = E.Engine(0)
+        ins, outs = (self.h_in, self.h_out) if host else (self.d_in, self.d_out)
+        eng.work_items(self.gws, self.lws).scheduler(sched, params).workers(D, C)
+        eng.program(self.program(ins, outs))
+        return eng
+
+    def work_items(self):
+        return self.gws
+
+
+class Mandelbrot(Workload):
+    name = "mandelbrot"
+    sched = ("static", (), 1, 0)  # one package, one device of every resident CTA
+
+    def host_setup(self):
+        self.r = W.mandelbrot_region(1024, 1024, 256)
+        self.npx = self.r["width"] * self.r["height"]
+        self.lws = 256
+        self.gws = self.npx // 4
+
+    def setup(self):
+        torch = self.torch
+        self.host_setup()
+        self.d_in = []
+        self.d_out = [torch.zeros(self.npx, dtype=torch.int32, device="cuda")]
+        self.h_in = []
+        self.h_out = [torch.zeros(self.npx, dtype=torch.int32).pin_memory()]
+        self.config = dict(size="1024x1024", max_iter=256, scheduler="static, 1 package")
+
+    def program(self, ins, outs):
+        r = self.r
+        out = outs[0]
+        return self.E.Program("mandelbrot").out(out).args(out, r["width"], r["height"], r["x0"], r["y0"],
+                                                          r["dx"], r["dy"], r["max_iter"])
+
+    def after(self):
+        # algorithmic work: 8 FP32 operations per iteration (x^2, y^2, |z|^2, x^2-y^2, +cx, 2x, *y, +cy)
+        its = int(self.d_out[0].to(self.torch.int64).sum().item())
+        self.iterations = its
+        return dict(bound="alu", flops=8.0 * its, unit_name="pixels/s", units=self.npx)
+
+    def cpu_sample(self, O, threads):
+        r = self.r
+        t = time.perf_counter()
+        O.mandelbrot(r["width"], r["height"], np.float32(r["x0"]), np.float32(r["y0"]), np.float32(r["dx"]),
+                     np.float32(r["dy"]), r["max_iter"], rows=(0, 256), threads=threads)
+        return 256 / 1024, time.perf_counter() - t, "256 of 1024 rows"
+
+
+class Gaussian(Workload):
+    name = "gaussian"
+    sched = ("dynamic", (256,), 8, 0)  # 256 row packages over 8 devices of CTAs
+
+    def host_setup(self):
+        self.H = self.Wd = 8192
+        self.img = W.gaussian_image(self.H, self.Wd)
+        self.w = W.gaussian_weights(31, 5.0)
+        self.lws = 128
+        self.gws = self.H * self.Wd
+
+    def setup(self):
+        torch = self.torch
+        self.host_setup()
+        img = self.img
+        self.d_in = [torch.from_numpy(img).cuda(), torch.from_numpy(self.w).cuda()]
+        self.d_out = [torch.zeros(self.H * self.Wd, dtype=torch.float32, device="cuda")]
+        self.h_in = [torch.from_numpy(img).pin_memory(), torch.from_numpy(self.w).pin_memory()]
+        self.h_out = [torch.zeros(self.H * self.Wd, dtype=torch.float32).pin_memory()]
+        self.config = dict(size="8192x8192", taps=31, sigma=5, scheduler="dynamic, 256 packages")
+
+    def program(self, ins, outs):
+        x, w = ins
+        out = outs[0]
+        return self.E.Program("gaussian").in_(x).in_(w).out(out).args(x, w, out, self.Wd, self.H, 31)
+
+    def after(self):
+        # algorithmic: 62 FMAs per pixel (31 vertical + 31 horizontal), 8 bytes of HBM per pixel
+        npx = self.H * self.Wd
+        return dict(bound="alu", flops=2.0 * 62 * npx, bytes=8.0 * npx, unit_name="pixels/s", units=npx)
+
+    def cpu_sample(self, O, threads):
+        t = time.perf_counter()
+        O.gaussian(self.img, self.w, rows=(0, 256), threads=threads)
+        return 256 / self.H, time.perf_counter() - t, "256 of 8192 rows"
+
+
+WORKLOADS = [Mandelbrot, Gaussian]
+
+
+# ====================================================================== helpers
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def balance_of(stats):
+    """Sec. 7.3 balance T_FD / T_LD over devices (time from the first package start)."""
+    if len(stats) == 0:
+        return None
+    t0 = int(stats["t0_ns"].min())
+    fin = {}
+    for d, t1 in zip(stats["device"], stats["t1_ns"]):
+        fin[int(d)] = max(fin.get(int(d), 0), int(t1) - t0)
+    f = list(fin.values())
+    return (min(f) / max(f)) if len(f) > 1 and max(f) > 0 else 1.0
+
+
+def worker_efficiency(ws):
+    busy = ws["busy_ns"].astype(np.float64)
+    return float(busy.mean() / busy.max()) if len(busy) and busy.max() > 0 else None
+
+
+# ====================================================================== arms
+def run_ours(args):
+    import torch
+
+    import paper_1805_02755_gb300 as E
+    from paper_1805_02755_gb300 import build as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+
+    names = args.only.split(",") if args.only else None
+    wls = [cls(E, torch, local) for cls in WORKLOADS if names is None or cls.name in names]
+    for w in wls:
+        w.setup()
+        s, p, D, C = w.sched
+        w.eng = w.make_engine(s, p, D, C)
+        w.mono = w.make_engine("monolithic", ())
+        w.host = w.make_engine(s, p, D, C, host=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        flush.fill_(1.0)  # evict L2 (outside the timed events)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(wls) + 1)]
+        ev[0].record(stream)
+        for i, w in enumerate(wls):
+            w.eng.run()
+            ev[i + 1].record(stream)
+        record.append(ev)
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    recs = []
+    for _ in range(args.steps):
+        step(recs)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per = {w.name: [] for w in wls}
+    tot = []
+    for ev in recs:
+        tot.append(ev[0].elapsed_time(ev[-1]))
+        for i, w in enumerate(wls):
+            per[w.name].append(ev[i].elapsed_time(ev[i + 1]))
+    step_ms = sum(tot) / len(tot)
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    launches = len(wls)  # one persistent launch per program
+
+    # scheduler overhead against the monolithic launch (same kernel body, no queue)
+    def timed(fn, n):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(n):
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    kern = {}
+    dominant = None
+    for w in wls:
+        ms = statistics.median(per[w.name])
+        ms_mono = timed(w.mono.run, max(5, args.steps))
+        ms_sched = timed(w.eng.run, max(5, args.steps))
+        alg = w.after()
+        st = w.eng.stats()
+        wst = w.eng.worker_stats()
+        info = w.eng.plan_info()
+        d = dict(ms=ms, work_items=w.work_items(), work_items_per_s=w.work_items() / (ms * 1e-3),
+                 config=w.config, plan=info, overhead_vs_monolithic_pct=100.0 * (ms_sched - ms_mono) / ms_mono,
+                 ms_monolithic=ms_mono, ms_scheduled_isolated=ms_sched,
+                 balance_T_FD_over_T_LD=balance_of(st), cta_busy_efficiency=worker_efficiency(wst),
+                 packages=len(st))
+        d[alg["unit_name"]] = alg["units"] / (ms * 1e-3)
+        if alg["bound"] == "alu":
+            peak = fp32_peak_tflops(sms, peaks["sm_max_mhz"])
+            ach = alg["flops"] / (ms * 1e-3) / 1e12
+            d["roofline"] = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak)
+            if "bytes" in alg:
+                gbs = alg["bytes"] / (ms * 1e-3) / 1e9
+                d["hbm"] = dict(achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=gbs / peaks["hbm_gbs"])
+        elif alg["bound"] == "hbm":
+            ach = alg["bytes"] / (ms * 1e-3) / 1e9
+            d["roofline"] = dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                                 frac=ach / peaks["hbm_gbs"])
+        else:
+            ach = alg["flops"] / (ms * 1e-3) / 1e12
+            pk = peaks["bf16_tflops"]
+            d["roofline"] = dict(bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk)
+        kern[w.name] = d
+        if dominant is None or ms > kern[dominant]["ms"]:
+            dominant = w.name
+
+    # end to end through host (pinned) buffers: the engine copies in, runs, copies out
+    h2d = sum(t.numel() * t.element_size() for w in wls for t in w.h_in)
+    d2h = sum(t.numel() * t.element_size() for w in wls for t in w.h_out)
+    for _ in range(max(1, args.warmup)):
+        for w in wls:
+            w.host.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for w in wls:
+            w.host.run()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+
+    total_wi = sum(w.work_items() for w in wls)
+    value = total_wi * world / (step_ms * 1e-3)
+    rf = dict(kern[dominant]["roofline"])
+    rf["kernel"] = dominant
+    rf["traffic"] = None
+    rf["peak_source"] = peaks["src"] if rf["bound"] != "alu" else \
+        "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (sms, peaks["sm_max_mhz"])
+    out = {
+        "metric": METRIC, "value": value, "unit": "work-items/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, shaped like the paper's workloads)",
+        "config": {"workload": "+".join(w.name for w in wls), "programs": {w.name: w.config for w in wls},
+                   "l2": "flushed (512 MiB write) before every step", "parallelism": "replicas"},
+        "e2e": {"value": total_wi * world / e2e_s, "unit": "work-items/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "roofline": rf,
+        "clocks": clk,
+        "kernels": kern,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(wls, total_wi, args)
+    if rank == 0:
+        print(json.dumps(out))
+    for w in wls:
+        w.eng.close()
+        w.mono.close()
+        w.host.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(wls, total_wi, args):
+    """Oracle on the host cores: a bounded sample of each program, scaled to the full step."""
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    full_s = 0.0
+    samples = []
+    for w in wls:
+        frac, secs, what = w.cpu_sample(oracle, threads)
+        full_s += secs / frac
+        samples.append("%s: %s in %.2fs" % (w.name, what, secs))
+    return dict(value=total_wi / full_s, unit="work-items/s", cores=threads, kind="oracle",
+                sample="; ".join(samples))
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle timed on this configuration."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+
+    names = args.only.split(",") if args.only else None
+    wls = []
+    for cls in WORKLOADS:
+        if names is None or cls.name in names:
+            w = cls(None, None, 0)
+            w.host_setup()
+            wls.append(w)
+    total_wi = sum(w.gws for w in wls)
+    times = []
+    what = {}
+    for i in range(args.warmup + args.steps):
+        full = 0.0
+        for w in wls:
+            frac, secs, desc = w.cpu_sample(oracle, threads)
+            what[w.name] = desc
+            full += secs / frac
+        if i >= args.warmup:
+            times.append(full)
+    step_s = statistics.median(times)
+    val = total_wi / step_s
+    samples = "; ".join("%s: %s" % kv for kv in what.items())
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "work-items/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "+".join(w.name for w in wls)},
+        "cpu_baseline": {"value": val, "unit": "work-items/s", "cores": threads, "kind": "oracle",
+                         "sample": samples + " (each step: bounded samples scaled to the full step)"},
+        "e2e": {"value": val, "unit": "work-items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--only", default="")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

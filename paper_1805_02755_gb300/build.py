@@ -24,6 +24,7 @@ SOURCES = {
     "runtime.cu": [],
     "registry.cu": [],
     "k_mandelbrot.cu": ["-fmad=false"],
+    "k_gaussian.cu": [],
 }
 HEADERS = ["ecl_internal.h", "sched.cuh"]
 

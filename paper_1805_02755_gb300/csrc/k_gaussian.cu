@@ -1,0 +1,406 @@
+// Separable Gaussian blur (Table 2: lws 128, image + filter-weight buffers,
+// out pattern 1:1), clamp-to-edge borders, FP32.
+//
+// Work-item g produces pixel g of the row-major image, so a package of
+// work-groups is a range of pixels: a band of rows with possibly partial
+// first and last rows.  The kernel splits a package into chunks of
+// (32-row band) x (256-column tile).  A chunk runs the vertical pass first
+// (one thread per column of the tile plus its 2r halo columns; the 32
+// outputs of a column slide down the input rows in registers, every input
+// value read once from global memory) into a shared-memory tile, then the
+// horizontal pass (four consecutive outputs per thread, 128-bit shared
+// loads and 128-bit stores).  Only pixels inside the package's range are
+// written, so packages that split a row are handled exactly.
+//
+// The 31-tap case has a fully unrolled path with the weights in
+// registers; other odd tap counts up to 63 use a plain loop path.
+#include <cuda_runtime.h>
+
+#include "ecl_internal.h"
+#include "sched.cuh"
+
+namespace ecl {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kRB = 32;        // output rows per chunk
+constexpr int kTW = 256;       // output columns per chunk
+constexpr int kMaxTaps = 63;
+constexpr int kSW = kTW + 32;  // shared tile width: 256 + 2*15 halo, padded to 9 warps
+
+struct GaussParams {
+    const float *in;
+    const float *w;
+    float *out;
+    int64_t W, H;
+    int32_t taps;
+    uint32_t lws;
+};
+
+struct ChunkGeom {
+    int64_t p0, p1;    // pixel range of the package
+    int64_t y0, rows;  // band
+    int64_t x0;        // tile
+};
+
+__host__ __device__ inline uint32_t gauss_nchunks(const GaussParams &p, uint64_t off, uint64_t len)
+{
+    const int64_t npx = p.W * p.H;
+    const int64_t p0 = (int64_t)(off * p.lws);
+    int64_t p1 = (int64_t)((off + len) * p.lws);
+    if (p1 > npx) p1 = npx;
+    if (p0 >= p1) return 0;
+    const int64_t r0 = p0 / p.W, r1 = (p1 - 1) / p.W;
+    const int64_t nb = (r1 - r0 + kRB) / kRB;
+    const int64_t nt = (p.W + kTW - 1) / kTW;
+    return (uint32_t)(nb * nt);
+}
+
+__device__ __forceinline__ ChunkGeom geom(const GaussParams &p, uint64_t off, uint64_t len, uint32_t t)
+{
+    ChunkGeom g;
+    const int64_t npx = p.W * p.H;
+    g.p0 = (int64_t)(off * p.lws);
+    g.p1 = (int64_t)((off + len) * p.lws);
+    if (g.p1 > npx) g.p1 = npx;
+    const int64_t r0 = g.p0 / p.W, r1 = (g.p1 - 1) / p.W;
+    const int64_t nt = (p.W + kTW - 1) / kTW;
+    const int64_t b = t / nt, c = t % nt;
+    g.y0 = r0 + b * kRB;
+    g.rows = min((int64_t)kRB, r1 + 1 - g.y0);
+    g.x0 = c * kTW;
+    return g;
+}
+
+__device__ __forceinline__ int64_t clampl(int64_t v, int64_t lo, int64_t hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Horizontal pass + store for one chunk.  Shared tile row o, column c holds
+// the vertical result at image column x0 - BASE + c (row stride SW floats).
+// T > 0: unrolled with the weights in registers; T == 0: any tap count,
+// weights in shared memory.
+template <int T, int SW, int BASE>
+__device__ __forceinline__ void horizontal_store(const GaussParams &p, const ChunkGeom &g, const float *sv,
+                                                 const float *wreg, const float *wsh)
+{
+    const int taps = T ? T : p.taps;
+    const int r = taps / 2;
+    const int cb = threadIdx.x % (kTW / 4);        // 4-column block
+    const int rsub = threadIdx.x / (kTW / 4);      // 4 rows at a time
+    const int64_t x = g.x0 + 4 * cb;
+    const bool vec = (p.W % 4) == 0;
+    for (int o = rsub; o < g.rows; o += kBlock / (kTW / 4)) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float *row = sv + o * SW + 4 * cb + (BASE - r);  // T == 0 path
+        if (T) {
+            // aligned 128-bit loads from column 4*cb + OFF0, values shifted by OFFR
+            constexpr int OFF = BASE - (T ? T : 1) / 2;
+            constexpr int OFF0 = OFF & ~3, OFFR = OFF & 3;
+            constexpr int NV = (OFFR + T + 3 + 3) / 4 * 4;
+            const float *arow = sv + o * SW + 4 * cb + OFF0;
+            float v[NV];
+#pragma unroll
+            for (int q = 0; q < NV / 4; ++q) {
+                const float4 f = *reinterpret_cast<const float4 *>(arow + 4 * q);
+                v[4 * q] = f.x;
+                v[4 * q + 1] = f.y;
+                v[4 * q + 2] = f.z;
+                v[4 * q + 3] = f.w;
+            }
+#pragma unroll
+            for (int u = 0; u < (T ? T : 1); ++u)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fmaf(wreg[u], v[OFFR + j + u], acc[j]);
+        } else {
+            for (int u = 0; u < taps; ++u) {
+                const float wu = wsh[u];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fmaf(wu, row[j + u], acc[j]);
+            }
+        }
+        const int64_t y = g.y0 + o;
+        const int64_t lin = y * p.W + x;
+        if (vec && x + 3 < p.W && lin >= g.p0 && lin + 3 < g.p1) {
+            *reinterpret_cast<float4 *>(p.out + lin) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + j < p.W && lin + j >= g.p0 && lin + j < g.p1) p.out[lin + j] = acc[j];
+        }
+    }
+}
+
+// 31-tap path.  The chunk's input tile (62 rows x 288 columns: image
+// columns x0-16 .. x0+271, rows clamped to the image) is staged in shared
+// memory with 16-byte cp.async copies (element-wise clamped loads at the
+// left/right borders).  The vertical pass then reads shared memory at
+// compile-time offsets, with the 31 weights and the 32 outputs of a column
+// in registers; its results overwrite the staged rows and feed the
+// horizontal pass.
+constexpr int kNIN = kRB + 30;   // staged input rows
+constexpr int kSC = kSW / 4;     // 16-byte chunks per staged row
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+struct Gauss31Body {
+    using Params = GaussParams;
+    Params p;
+    float (*st)[kSW];  // [kNIN][kSW] staged input, then [kRB][kSW] vertical results
+    float wr[31];
+
+    static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t off, uint64_t len)
+    {
+        return gauss_nchunks(q, off, len);
+    }
+
+    __device__ __forceinline__ void stage(const ChunkGeom &g)
+    {
+        const bool vec_ok = (p.W % 4) == 0 && ((uintptr_t)p.in % 16) == 0;
+        for (int q = threadIdx.x; q < kNIN * kSC; q += kBlock) {
+            const int k = q / kSC, c4 = q % kSC;
+            const int64_t ys = clampl(g.y0 - 15 + k, 0, p.H - 1);
+            const int64_t xs = g.x0 - 16 + 4 * c4;
+            const float *row = p.in + ys * p.W;
+            float *dst = &st[k][4 * c4];
+            if (vec_ok && xs >= 0 && xs + 4 <= p.W) {
+                cp_async16(dst, row + xs);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dst[j] = __ldg(row + clampl(xs + j, 0, p.W - 1));
+            }
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t len, uint32_t t, uint32_t)
+    {
+        const ChunkGeom g = geom(p, off, len, t);
+        stage(g);
+        __syncthreads();
+        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+        // vertical pass: staged column c <-> image column x0 - 16 + c
+        float acc[kRB];
+        float acc2[kRB];
+        const int c1 = warp * 32 + lane;
+        const bool two = (warp == 0);  // 9 column-warps over 8 warps
+        const int c2 = 8 * 32 + lane;
+#pragma unroll
+        for (int o = 0; o < kRB; ++o) acc[o] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kNIN; ++k) {
+            const float v = st[k][c1];
+#pragma unroll
+            for (int o = 0; o < kRB; ++o)
+                if (k - o >= 0 && k - o < 31) acc[o] = fmaf(wr[k - o], v, acc[o]);
+        }
+        if (two) {
+#pragma unroll
+            for (int o = 0; o < kRB; ++o) acc2[o] = 0.f;
+#pragma unroll
+            for (int k = 0; k < kNIN; ++k) {
+                const float v = st[k][c2];
+#pragma unroll
+                for (int o = 0; o < kRB; ++o)
+                    if (k - o >= 0 && k - o < 31) acc2[o] = fmaf(wr[k - o], v, acc2[o]);
+            }
+        }
+        __syncthreads();  // every staged row has been read
+#pragma unroll
+        for (int o = 0; o < kRB; ++o) st[o][c1] = acc[o];
+        if (two) {
+#pragma unroll
+            for (int o = 0; o < kRB; ++o) st[o][c2] = acc2[o];
+        }
+        __syncthreads();
+        // horizontal pass: output x needs vertical results at staged columns x - x0 + 1 .. + 31
+        horizontal_store<31, kSW, 16>(p, g, &st[0][0], wr, nullptr);
+        __syncthreads();
+    }
+};
+
+// Any odd tap count up to 63: plain loops, weights in shared memory.  Shared
+// tile column c holds image column x0 - 31 + c (room for radius 31).
+constexpr int kSWA = kTW + 64;
+
+struct GaussAnyBody {
+    using Params = GaussParams;
+    Params p;
+    float *sv;  // [kRB][kSWA]
+    const float *wsh;
+
+    static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t off, uint64_t len)
+    {
+        return gauss_nchunks(q, off, len);
+    }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t len, uint32_t t, uint32_t)
+    {
+        const ChunkGeom g = geom(p, off, len, t);
+        const int r = p.taps / 2;
+        for (int c = threadIdx.x; c < kTW + 2 * r; c += kBlock) {
+            const int col = c + (31 - r);
+            const int64_t xs = clampl(g.x0 - r + c, 0, p.W - 1);
+            for (int o = 0; o < g.rows; ++o) {
+                float acc = 0.f;
+                for (int v = 0; v < p.taps; ++v) {
+                    const int64_t ys = clampl(g.y0 + o - r + v, 0, p.H - 1);
+                    acc = fmaf(wsh[v], __ldg(p.in + ys * p.W + xs), acc);
+                }
+                sv[o * kSWA + col] = acc;
+            }
+        }
+        __syncthreads();
+        horizontal_store<0, kSWA, 31>(p, g, sv, nullptr, wsh);
+        __syncthreads();
+    }
+};
+
+__global__ void __launch_bounds__(kBlock) k_gauss31(GaussParams prm, SchedArgs s)
+{
+    extern __shared__ __align__(16) float smem_g[];
+    Gauss31Body b;
+    b.p = prm;
+    b.st = reinterpret_cast<float(*)[kSW]>(smem_g);
+#pragma unroll
+    for (int u = 0; u < 31; ++u) b.wr[u] = __ldg(prm.w + u);
+    drive(s, b);
+}
+
+__global__ void __launch_bounds__(kBlock) k_gauss_any(GaussParams prm, SchedArgs s)
+{
+    __shared__ __align__(16) float sv[kRB][kSWA];
+    __shared__ float wsh[kMaxTaps];
+    for (int u = threadIdx.x; u < prm.taps; u += blockDim.x) wsh[u] = prm.w[u];
+    __syncthreads();
+    GaussAnyBody b;
+    b.p = prm;
+    b.sv = &sv[0][0];
+    b.wsh = wsh;
+    drive(s, b);
+}
+
+GaussParams params_of(const KArgs &a, uint32_t lws)
+{
+    GaussParams p;
+    p.in = a.buf<const float>(0);
+    p.w = a.buf<const float>(1);
+    p.out = a.buf<float>(2);
+    p.W = a.i32(3);
+    p.H = a.i32(4);
+    p.taps = a.i32(5);
+    p.lws = lws;
+    return p;
+}
+
+ecl_status validate(const KArgs &a, uint64_t gws, uint32_t, std::string &err)
+{
+    const int64_t W = a.i32(3), H = a.i32(4), T = a.i32(5);
+    if (W <= 0 || H <= 0) {
+        err = "width and height must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (T < 1 || T > kMaxTaps || T % 2 == 0) {
+        err = "taps must be odd, 1..63";
+        return ECL_ERR_ARG;
+    }
+    const uint64_t npx = (uint64_t)W * (uint64_t)H;
+    if (a.bytes[0] < npx * 4 || a.bytes[2] < npx * 4) {
+        err = "image buffers smaller than width*height floats";
+        return ECL_ERR_BUFFER;
+    }
+    if (a.bytes[1] < (uint64_t)T * 4) {
+        err = "weight buffer smaller than taps floats";
+        return ECL_ERR_BUFFER;
+    }
+    if ((uintptr_t)a.ptr[2] % 16) {
+        err = "output buffer must be 16-byte aligned";
+        return ECL_ERR_BUFFER;
+    }
+    if (gws < npx) {
+        err = "the NDRange (one pixel per work-item) does not cover the image";
+        return ECL_ERR_SIZE;
+    }
+    return ECL_OK;
+}
+
+uint64_t grain(const KArgs &, uint64_t, uint32_t) { return 1; }
+
+uint32_t nchunks(const KArgs &a, uint64_t, uint32_t lws, uint64_t off, uint64_t len)
+{
+    return gauss_nchunks(params_of(a, lws), off, len);
+}
+
+constexpr size_t kSmem31 = sizeof(float) * kNIN * kSW;
+
+bool set_smem_attr()
+{
+    static bool done = false;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_gauss31, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem31) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        done = true;
+    }
+    return true;
+}
+
+int ctas_per_sm()
+{
+    if (!set_smem_attr()) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gauss31, kBlock, kSmem31) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    const GaussParams p = params_of(a, c.lws);
+    if (p.taps == 31) {
+        if (!set_smem_attr()) {
+            err = "cannot raise the shared-memory limit";
+            return ECL_ERR_CUDA;
+        }
+        k_gauss31<<<c.grid, kBlock, kSmem31, c.stream>>>(p, s);
+    } else {
+        // the generic path keeps a smaller resident count; the plan used the fast path's
+        // count, so it is clamped here: more CTAs than resident is still correct
+        k_gauss_any<<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    }
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
+}
+
+}  // namespace
+
+extern const KernelDesc kGaussian = {
+    "gaussian",
+    6,
+    {{"in", A_BUF_IN}, {"weights", A_BUF_IN}, {"out", A_BUF_OUT}, {"width", A_I32}, {"height", A_I32},
+     {"taps", A_I32}},
+    1,
+    1,
+    kBlock,
+    0,
+    validate,
+    grain,
+    nchunks,
+    ctas_per_sm,
+    launch,
+};
+
+}  // namespace ecl

@@ -7,9 +7,11 @@
 namespace ecl {
 
 extern const KernelDesc kMandelbrot;
+extern const KernelDesc kGaussian;
 
 static const KernelDesc *const kAll[] = {
     &kMandelbrot,
+    &kGaussian,
 };
 
 const KernelDesc *find_kernel(const char *name)

@@ -36,7 +36,7 @@ __device__ __forceinline__ uint32_t smid()
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
 {
     unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 

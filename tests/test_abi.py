@@ -11,7 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-KERNELS = ["mandelbrot"]
+KERNELS = ["mandelbrot", "gaussian"]
 
 
 @pytest.fixture(scope="module")

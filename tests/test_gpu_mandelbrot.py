@@ -132,7 +132,8 @@ def test_repeated_runs_reset_the_queue(E, torch, oracle_mod):
         eng.run()
         eng.synchronize()
         assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(H, Wd), ref)
-        assert len(eng.stats()) == 33
+        # Dynamic: ceil(256 / 33) = 8 work-groups per package -> 32 packages
+        assert len(eng.stats()) == len(OS.dynamic(Wd * H // 1024, 33)) == 32
     # switching scheduler on the same engine re-plans
     eng.scheduler("hguided", (2.0, 1.0)).workers(0, 0)
     out.zero_()
