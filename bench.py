@@ -162,7 +162,165 @@ class Gaussian(Workload):
         return 256 / self.H, time.perf_counter() - t, "256 of 8192 rows"
 
 
-WORKLOADS = [Mandelbrot, Gaussian]
+class NBody(Workload):
+    """Config 3: force (HGuided), potential energy (FP64 sums), its adjoint and
+    the finite-difference check, four launches over the same 65536 bodies."""
+    name = "nbody"
+    sched = ("hguided", (2.0, 1.0), 8, 0)
+    EPS2 = 1e-3
+    NFD = 256
+
+    def host_setup(self):
+        self.n = 65536
+        self.pos, _ = W.nbody_bodies(self.n)
+        self.lws = 64
+        self.gws = self.n
+        rng = W.rng(W.SEED_BASE + 20)
+        self.fd_body = rng.choice(self.n, self.NFD, replace=False).astype(np.int32)
+        self.fd_comp = rng.integers(0, 3, self.NFD).astype(np.int32)
+
+    def setup(self):
+        torch = self.torch
+        self.host_setup()
+        n = self.n
+        pos = torch.from_numpy(self.pos)
+        gE = torch.ones(1, dtype=torch.float32)
+        fb, fc = torch.from_numpy(self.fd_body), torch.from_numpy(self.fd_comp)
+        self.d_in = [pos.cuda(), gE.cuda(), fb.cuda(), fc.cuda()]
+        self.d_out = [torch.zeros((n, 4), device="cuda"), torch.zeros(1, dtype=torch.float64, device="cuda"),
+                      torch.zeros((n, 4), device="cuda"), torch.zeros(self.NFD, dtype=torch.float64, device="cuda")]
+        self.h_in = [pos.pin_memory(), gE.pin_memory(), fb.pin_memory(), fc.pin_memory()]
+        self.h_out = [torch.zeros((n, 4)).pin_memory(), torch.zeros(1, dtype=torch.float64).pin_memory(),
+                      torch.zeros((n, 4)).pin_memory(), torch.zeros(self.NFD, dtype=torch.float64).pin_memory()]
+        self.config = dict(bodies=n, eps2=self.EPS2, lws=64, scheduler="hguided k=2 over 8 devices",
+                           programs="nbody_acc + nbody_energy + nbody_adjoint + nbody_fd(256 samples, h=1e-3)")
+
+    def make_engine(self, sched, params, D=0, C=0, host=False):
+        E = self.E
+        ins, outs = (self.h_in, self.h_out) if host else (self.d_in, self.d_out)
+        pos, gE, fb, fc = ins
+        acc, en, grad, fd = outs
+        n = self.n
+        progs = [
+            (E.Program("nbody_acc").in_(pos).out(acc).args(pos, n, self.EPS2, acc), n, 64),
+            (E.Program("nbody_energy").in_(pos).out(en).args(pos, n, self.EPS2, en), n, 64),
+            (E.Program("nbody_adjoint").in_(pos).in_(gE).out(grad).args(pos, n, self.EPS2, gE, grad), n, 64),
+            (E.Program("nbody_fd").in_(pos).in_(fb).in_(fc).out(fd)
+             .args(pos, n, self.EPS2, 1e-3, fb, fc, self.NFD, fd), self.NFD, 1),
+        ]
+        return MultiEngine(E, progs, sched, params, D, C)
+
+    def work_items(self):
+        return 3 * self.n + self.NFD
+
+    def after(self):
+        n = self.n
+        # FP32 flops per pair (FMA = 2): force 18, energy (i<j) 11, adjoint 20
+        flops = 18.0 * n * n + 11.0 * n * (n - 1) / 2 + 20.0 * n * n
+        return dict(bound="alu", flops=flops, unit_name="interactions/s", units=2 * n * n + n * (n - 1) // 2)
+
+    def cpu_sample(self, O, threads):
+        t = time.perf_counter()
+        O.nbody_acc(self.pos, self.EPS2, bodies=(0, 128), threads=threads)
+        O.nbody_energy_grad(self.pos, self.EPS2, bodies=(0, 128), threads=threads)
+        O.nbody_potential(self.pos, self.EPS2, bodies=(0, 128), threads=threads)
+        secs = time.perf_counter() - t
+        # acc + grad rows are each 1/n of their program; the potential stands in for the energy rows
+        return 128 / self.n, secs, "128 of 65536 bodies of the force, adjoint and potential rows"
+
+
+class Binomial(Workload):
+    """Config 4: 2^20 European options of depth U{256..2048}, price + delta + vega in one launch."""
+    name = "binomial"
+    sched = ("hguided", (2.0, 1.0), 8, 0)
+
+    def host_setup(self):
+        self.n = 1 << 20
+        self.o = W.binomial_options(self.n)
+        self.lws = 32
+        self.gws = self.n * 32
+        st = self.o["steps"].astype(np.int64)
+        self.nodes = int((st * (st + 1) // 2).sum())
+
+    def setup(self):
+        torch = self.torch
+        self.host_setup()
+        o = self.o
+        ts = [torch.from_numpy(np.ascontiguousarray(o[k])) for k in ("S", "K", "T", "sigma", "steps")]
+        self.d_in = [t.cuda() for t in ts]
+        self.d_out = [torch.zeros(self.n, device="cuda"), torch.zeros((self.n, 2), device="cuda")]
+        self.h_in = [t.pin_memory() for t in ts]
+        self.h_out = [torch.zeros(self.n).pin_memory(), torch.zeros((self.n, 2)).pin_memory()]
+        self.config = dict(options=self.n, steps="U{256..2048}", scheduler="hguided k=2 over 8 devices",
+                           outputs="price + delta + vega", node_updates=self.nodes)
+
+    def program(self, ins, outs, greeks=True):
+        S, K, T, sig, st = ins
+        price, gr = outs
+        p = self.E.Program("binomial")
+        for t in ins:
+            p.in_(t)
+        p.out(price)
+        if greeks:
+            p.out(gr)
+        return p.args(S, K, T, sig, st, self.o["r"], self.n, price, gr if greeks else None)
+
+    def plain_engine(self):
+        E = self.E
+        eng = E.Engine(0)
+        s, prm, D, C = self.sched
+        eng.work_items(self.gws, self.lws).scheduler(s, prm).workers(D, C)
+        eng.program(self.program(self.d_in, self.d_out, greeks=False))
+        return eng
+
+    def after(self):
+        # FP32 flops per node update: price 4 (add, sub, FMA), delta 4, vega 6
+        return dict(bound="alu", flops=14.0 * self.nodes, unit_name="options/s", units=self.n,
+                    extra={"node_updates_per_s": self.nodes})
+
+    def cpu_sample(self, O, threads):
+        t = time.perf_counter()
+        k = 4 * threads
+        o = self.o
+        O.binomial(o["S"][:k], o["K"][:k], o["T"][:k], o["sigma"][:k], o["steps"][:k], o["r"], threads=threads)
+        return k / self.n, time.perf_counter() - t, "%d of %d options (price, delta, vega)" % (k, self.n)
+
+
+class MultiEngine:
+    """Several programs of one configuration, each on its own engine, run in order."""
+
+    def __init__(self, E, progs, sched, params, D, C):
+        self.engs = []
+        for prog, gws, lws in progs:
+            e = E.Engine(0)
+            e.work_items(gws, lws).scheduler(sched, params).workers(D if lws > 1 else 0, C if lws > 1 else 0)
+            e.program(prog)
+            self.engs.append(e)
+
+    def run(self):
+        for e in self.engs:
+            e.run()
+        return self
+
+    def stats(self):
+        return self.engs[0].stats()
+
+    def worker_stats(self):
+        return self.engs[0].worker_stats()
+
+    def plan_info(self):
+        return self.engs[0].plan_info()
+
+    def close(self):
+        for e in self.engs:
+            e.close()
+
+    @property
+    def launches(self):
+        return len(self.engs)
+
+
+WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial]
 
 
 # ====================================================================== helpers
@@ -293,7 +451,7 @@ def run_ours(args):
         t = torch.tensor([step_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_ms = float(t.item())
-    launches = len(wls)  # one persistent launch per program
+    launches = sum(getattr(w.eng, "launches", 1) for w in wls)  # one persistent launch per program
 
     # scheduler overhead against the monolithic launch (same kernel body, no queue)
     def timed(fn, n):
@@ -325,6 +483,14 @@ def run_ours(args):
                  balance_T_FD_over_T_LD=balance_of(st), cta_busy_efficiency=worker_efficiency(wst),
                  packages=len(st))
         d[alg["unit_name"]] = alg["units"] / (ms * 1e-3)
+        for k2, v2 in alg.get("extra", {}).items():
+            d[k2] = v2 / (ms * 1e-3)
+        if hasattr(w, "plain_engine"):  # the plain form beside the adjoint form
+            pe = w.plain_engine()
+            ms_plain = timed(pe.run, max(3, min(args.steps, 5)))
+            d["plain_ms"] = ms_plain
+            d["adjoint_over_plain"] = ms / ms_plain
+            pe.close()
         if alg["bound"] == "alu":
             peak = fp32_peak_tflops(sms, peaks["sm_max_mhz"])
             ach = alg["flops"] / (ms * 1e-3) / 1e12

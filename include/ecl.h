@@ -18,9 +18,9 @@
  *  - Pointers are plain host or device addresses; sizes are in bytes unless
  *    stated.  No call takes or returns a framework type.
  *  - Every call returns an ecl_status.  Errors are never thrown and never
- *    end the process.  The first error of an engine is latched with a text
- *    that ecl_last_error() returns (the has_errors/get_errors analogue of
- *    Listing 1).  A NULL handle gives ECL_ERR_ARG.
+ *    end the process.  An engine counts its errors and keeps the text of
+ *    the most recent one for ecl_last_error() (the has_errors/get_errors
+ *    analogue of Listing 1).  A NULL handle gives ECL_ERR_ARG.
  *  - The caller owns every buffer it registers; the engine owns the
  *    programs given to it, its package table, queue and statistics memory,
  *    and the device mirrors it makes for host buffers.
@@ -187,8 +187,8 @@ ecl_status ecl_plan(ecl_sched_kind kind, const double *params, int nparams, uint
                     uint32_t devices, uint64_t *off, uint64_t *len, uint32_t *device, size_t cap,
                     size_t *n, char *errbuf, size_t errlen);
 
-/* Text of the first error latched on the engine ("" when none).  The
- * pointer stays valid until the engine is destroyed or the error cleared. */
+/* Text of the most recent error of the engine ("" when none).  The pointer
+ * stays valid until the next failing call, ecl_clear_errors or destroy. */
 const char *ecl_last_error(const ecl_engine *e);
 
 /* Number of errors seen since creation or the last clear, and clearing. */
@@ -285,11 +285,12 @@ const char *ecl_kernel_name(int i);
  *     4 B body int32[s]  5 B comp int32[s]  6 S int32 s  7 B out double[s]
  *   central difference of E in coordinate comp of body: the perturbed
  *   coordinate is rounded to FP32 and the denominator is the FP32 distance
- *   between the two placements; FP32 terms, FP64 sums.
+ *   between the two placements; FP32 terms, FP64 sums.  A sample with a
+ *   body outside [0, n) or a component outside 0..2 gives NaN.
  *
  * "binomial"  Listing 1 workload (9 args, out pattern 1:32, lws 32)
  *     0 B S float[n]  1 B K float[n]  2 B T float[n]  3 B sigma float[n]
- *     4 B steps int32[n] (1..2048)  5 S float r  6 S int32 n
+ *     4 B steps int32[n] (1..2048; other depths give NaN)  5 S float r  6 S int32 n
  *     7 B price float[n]  8 B greeks float2[n] (delta, vega) or NULL
  *   European call on a Cox-Ross-Rubinstein lattice of steps[o] steps,
  *   backward induction in FP32 by one warp per option; with greeks the

@@ -63,6 +63,7 @@ def lib():
             L.ecl_oracle_nbody_energy_row.argtypes = [_p, _i64, _f64, _i64, _p]
             L.ecl_oracle_nbody_energy_row.restype = _f64
             L.ecl_oracle_nbody_energy_grad.argtypes = [_p, _i64, _f64, _p, _i64, _i64]
+            L.ecl_oracle_nbody_potential.argtypes = [_p, _i64, _f64, _p, _i64, _i64]
             L.ecl_oracle_binomial.argtypes = [_p, _p, _p, _p, _p, _f64, _i32, _i64, _i64, _p, _p, _p]
             L.ecl_oracle_bf16_round.argtypes = [_f32]
             L.ecl_oracle_bf16_round.restype = _f32
@@ -189,6 +190,18 @@ def nbody_energy_grad(pos4: np.ndarray, eps2: float, bodies=None,
     _run(lambda i0, i1: L.ecl_oracle_nbody_energy_grad(_ptr(pos4), n, eps2, _ptr(g), i0, i1),
          b, e, threads)
     return g
+
+
+def nbody_potential(pos4: np.ndarray, eps2: float, bodies=None,
+                    threads: Optional[int] = None) -> np.ndarray:
+    """phi_i = sum_{j != i} m_j / sqrt(r_ij^2 + eps2) (so dE/dm_i = -phi_i)."""
+    L = lib()
+    pos4 = _c(pos4, np.float32)
+    n = pos4.shape[0]
+    phi = np.zeros(n, dtype=np.float64)
+    b, e = bodies if bodies is not None else (0, n)
+    _run(lambda i0, i1: L.ecl_oracle_nbody_potential(_ptr(pos4), n, eps2, _ptr(phi), i0, i1), b, e, threads)
+    return phi
 
 
 def nbody_fd_energy_grad(pos4: np.ndarray, eps2: float, idx, comp, h: float):

@@ -233,6 +233,25 @@ void ecl_oracle_nbody_energy_grad(const float *pos4, int64_t n, double eps2,
     }
 }
 
+/* Potential of body i: phi_i = sum_{j != i} m_j / sqrt(|r_i - r_j|^2 + eps2),
+ * so that dE/dm_i = -phi_i and sum_i m_i phi_i = -2E. */
+void ecl_oracle_nbody_potential(const float *pos4, int64_t n, double eps2, double *phi,
+                                int64_t i_begin, int64_t i_end)
+{
+    for (int64_t i = i_begin; i < i_end; ++i) {
+        const double xi = pos4[4 * i], yi = pos4[4 * i + 1], zi = pos4[4 * i + 2];
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double dx = xi - (double)pos4[4 * j];
+            const double dy = yi - (double)pos4[4 * j + 1];
+            const double dz = zi - (double)pos4[4 * j + 2];
+            s += (double)pos4[4 * j + 3] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+        }
+        phi[i] = s;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Binomial options (Listing 1 workload): Cox-Ross-Rubinstein lattice for a
  * European option, priced by backward induction, with the exact

@@ -25,6 +25,8 @@ SOURCES = {
     "registry.cu": [],
     "k_mandelbrot.cu": ["-fmad=false"],
     "k_gaussian.cu": [],
+    "k_nbody.cu": [],
+    "k_binomial.cu": [],
 }
 HEADERS = ["ecl_internal.h", "sched.cuh"]
 

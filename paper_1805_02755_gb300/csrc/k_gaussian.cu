@@ -24,9 +24,9 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kRB = 32;        // output rows per chunk
-constexpr int kTW = 256;       // output columns per chunk
+constexpr int kTW = 224;       // output columns per chunk (vertical pass: 256 columns = 8 warps)
 constexpr int kMaxTaps = 63;
-constexpr int kSW = kTW + 32;  // shared tile width: 256 + 2*15 halo, padded to 9 warps
+constexpr int kSW = kTW + 32;  // staged / vertical tile width: 224 + 2*15 halo + 2 pad = 256
 
 struct GaussParams {
     const float *in;
@@ -87,11 +87,11 @@ __device__ __forceinline__ void horizontal_store(const GaussParams &p, const Chu
 {
     const int taps = T ? T : p.taps;
     const int r = taps / 2;
-    const int cb = threadIdx.x % (kTW / 4);        // 4-column block
-    const int rsub = threadIdx.x / (kTW / 4);      // 4 rows at a time
-    const int64_t x = g.x0 + 4 * cb;
     const bool vec = (p.W % 4) == 0;
-    for (int o = rsub; o < g.rows; o += kBlock / (kTW / 4)) {
+    constexpr int NCB = kTW / 4;  // 4-column blocks per row
+    for (int q = threadIdx.x; q < g.rows * NCB; q += kBlock) {
+        const int o = q / NCB, cb = q % NCB;
+        const int64_t x = g.x0 + 4 * cb;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         const float *row = sv + o * SW + 4 * cb + (BASE - r);  // T == 0 path
         if (T) {
@@ -132,8 +132,8 @@ __device__ __forceinline__ void horizontal_store(const GaussParams &p, const Chu
     }
 }
 
-// 31-tap path.  The chunk's input tile (62 rows x 288 columns: image
-// columns x0-16 .. x0+271, rows clamped to the image) is staged in shared
+// 31-tap path.  The chunk's input tile (62 rows x 256 columns: image
+// columns x0-16 .. x0+239, rows clamped to the image) is staged in shared
 // memory with 16-byte cp.async copies (element-wise clamped loads at the
 // left/right borders).  The vertical pass then reads shared memory at
 // compile-time offsets, with the 31 weights and the 32 outputs of a column
@@ -162,13 +162,14 @@ struct Gauss31Body {
     __device__ __forceinline__ void stage(const ChunkGeom &g)
     {
         const bool vec_ok = (p.W % 4) == 0 && ((uintptr_t)p.in % 16) == 0;
-        for (int q = threadIdx.x; q < kNIN * kSC; q += kBlock) {
-            const int k = q / kSC, c4 = q % kSC;
+        const int c4 = threadIdx.x % kSC;  // fixed 16-byte column chunk per thread
+        const int64_t xs = g.x0 - 16 + 4 * c4;
+        const bool vec = vec_ok && xs >= 0 && xs + 4 <= p.W;
+        for (int k = threadIdx.x / kSC; k < kNIN; k += kBlock / kSC) {
             const int64_t ys = clampl(g.y0 - 15 + k, 0, p.H - 1);
-            const int64_t xs = g.x0 - 16 + 4 * c4;
             const float *row = p.in + ys * p.W;
             float *dst = &st[k][4 * c4];
-            if (vec_ok && xs >= 0 && xs + 4 <= p.W) {
+            if (vec) {
                 cp_async16(dst, row + xs);
             } else {
 #pragma unroll
@@ -183,13 +184,9 @@ struct Gauss31Body {
         const ChunkGeom g = geom(p, off, len, t);
         stage(g);
         __syncthreads();
-        const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-        // vertical pass: staged column c <-> image column x0 - 16 + c
+        // vertical pass: staged column c <-> image column x0 - 16 + c, one column per thread
         float acc[kRB];
-        float acc2[kRB];
-        const int c1 = warp * 32 + lane;
-        const bool two = (warp == 0);  // 9 column-warps over 8 warps
-        const int c2 = 8 * 32 + lane;
+        const int c1 = threadIdx.x;
 #pragma unroll
         for (int o = 0; o < kRB; ++o) acc[o] = 0.f;
 #pragma unroll
@@ -199,24 +196,9 @@ struct Gauss31Body {
             for (int o = 0; o < kRB; ++o)
                 if (k - o >= 0 && k - o < 31) acc[o] = fmaf(wr[k - o], v, acc[o]);
         }
-        if (two) {
-#pragma unroll
-            for (int o = 0; o < kRB; ++o) acc2[o] = 0.f;
-#pragma unroll
-            for (int k = 0; k < kNIN; ++k) {
-                const float v = st[k][c2];
-#pragma unroll
-                for (int o = 0; o < kRB; ++o)
-                    if (k - o >= 0 && k - o < 31) acc2[o] = fmaf(wr[k - o], v, acc2[o]);
-            }
-        }
         __syncthreads();  // every staged row has been read
 #pragma unroll
         for (int o = 0; o < kRB; ++o) st[o][c1] = acc[o];
-        if (two) {
-#pragma unroll
-            for (int o = 0; o < kRB; ++o) st[o][c2] = acc2[o];
-        }
         __syncthreads();
         // horizontal pass: output x needs vertical results at staged columns x - x0 + 1 .. + 31
         horizontal_store<31, kSW, 16>(p, g, &st[0][0], wr, nullptr);
@@ -261,7 +243,7 @@ struct GaussAnyBody {
     }
 };
 
-__global__ void __launch_bounds__(kBlock) k_gauss31(GaussParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock, 3) k_gauss31(GaussParams prm, SchedArgs s)
 {
     extern __shared__ __align__(16) float smem_g[];
     Gauss31Body b;

@@ -1,0 +1,593 @@
+// All-pairs NBody (Listing 2: float4 positions (x, y, z, m), softening passed
+// squared, lws 64, out pattern 1:1) and the potential-energy family built on
+// the same pair loop:
+//   nbody          one explicit step: in pos/vel -> out pos/vel
+//   nbody_acc      a_i = sum_j m_j d_ij / (|d_ij|^2 + eps2)^(3/2)
+//   nbody_adjoint  dL/dE * (dE/dr_i, dE/dm_i), dE/dr_i = -m_i a_i,
+//                  dE/dm_i = -sum_{j!=i} m_j / sqrt(|d_ij|^2 + eps2)
+//   nbody_energy   E = -sum_{i<j} m_i m_j / sqrt(|d_ij|^2 + eps2)
+//   nbody_fd       central differences of E in sampled coordinates
+//
+// One chunk = one work-group of lws bodies (lws 32..256, a power of two).
+// The CTA has 256 threads: thread t owns body t % lws of the work-group and
+// the j-slice t / lws; j-bodies are staged in shared memory 256 at a time
+// (tiles on an absolute 256-body grid).  Each thread sums the pair terms of
+// one tile in FP32, then adds the tile sum to its running FP32 total
+// (two-level summation); the slices of a body are added in slice order.
+// The energy and finite-difference sums are FP32 pair terms accumulated in
+// FP64, reduced in a fixed order, so results do not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include "ecl_internal.h"
+#include "sched.cuh"
+
+namespace ecl {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kTile = 256;
+
+enum NMode : uint32_t { NB_STEP = 0, NB_ACC = 1, NB_ADJ = 2 };
+
+struct NBodyParams {
+    const float4 *pos;
+    const float4 *vel;
+    int64_t n;
+    float dt, eps2;
+    float4 *out_pos, *out_vel;  // NB_STEP
+    float4 *out_acc;            // NB_ACC
+    const float *grad_E;        // NB_ADJ: device scalar dL/dE
+    float4 *out_grad;           // NB_ADJ
+    uint32_t lws;
+};
+
+__host__ __device__ inline uint32_t one_chunk_per_wg(uint64_t len) { return (uint32_t)len; }
+
+// Stage j-tile `tile` (zero-mass padding beyond n).
+__device__ __forceinline__ void stage_tile(float4 *sh, const float4 *pos, int64_t n, int64_t tile)
+{
+    const int64_t j = tile * kTile + threadIdx.x;
+    sh[threadIdx.x] = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <uint32_t MODE>
+struct ForceBody {
+    using Params = NBodyParams;
+    Params p;
+    float4 *sh;   // [kTile] j-bodies
+    float4 *red;  // [kBlock] slice partials
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
+    {
+        return one_chunk_per_wg(len);
+    }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const uint32_t lws = p.lws;
+        const uint32_t S = kBlock / lws;             // j-slices
+        const uint32_t b = threadIdx.x % lws, s = threadIdx.x / lws;
+        const int64_t i = (int64_t)(off + t) * lws + b;
+        const bool valid = i < p.n;
+        const float4 pi = valid ? __ldg(p.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t span = kTile / S;             // j's of one tile in this slice
+        float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;
+        const int64_t ntiles = (p.n + kTile - 1) / kTile;
+        for (int64_t tile = 0; tile < ntiles; ++tile) {
+            __syncthreads();
+            stage_tile(sh, p.pos, p.n, tile);
+            __syncthreads();
+            float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+            const float4 *q = sh + s * span;
+#pragma unroll 8
+            for (uint32_t k = 0; k < span; ++k) {
+                const float4 pj = q[k];
+                const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2)));
+                const float inv = rsqrtf(r2);
+                const float mi = pj.w * inv;
+                if (MODE == NB_ADJ) tp += mi;
+                const float sc = mi * (inv * inv);
+                tx = fmaf(sc, dx, tx);
+                ty = fmaf(sc, dy, ty);
+                tz = fmaf(sc, dz, tz);
+            }
+            ax += tx;
+            ay += ty;
+            az += tz;
+            if (MODE == NB_ADJ) pot += tp;
+        }
+        // combine the slices of each body in slice order
+        __syncthreads();
+        red[threadIdx.x] = make_float4(ax, ay, az, pot);
+        __syncthreads();
+        if (s == 0 && valid) {
+            float4 a = red[b];
+            for (uint32_t q = 1; q < S; ++q) {
+                const float4 r = red[q * lws + b];
+                a.x += r.x;
+                a.y += r.y;
+                a.z += r.z;
+                a.w += r.w;
+            }
+            if (MODE == NB_ACC) {
+                p.out_acc[i] = make_float4(a.x, a.y, a.z, 0.f);
+            } else if (MODE == NB_STEP) {
+                const float4 v = __ldg(p.vel + i);
+                const float h = 0.5f * p.dt * p.dt;
+                p.out_pos[i] = make_float4(pi.x + v.x * p.dt + a.x * h, pi.y + v.y * p.dt + a.y * h,
+                                           pi.z + v.z * p.dt + a.z * h, pi.w);
+                p.out_vel[i] = make_float4(v.x + a.x * p.dt, v.y + a.y * p.dt, v.z + a.z * p.dt, v.w);
+            } else {
+                // the self term j == i added m_i / sqrt(eps2) to the potential sum
+                const float self = pi.w * rsqrtf(p.eps2);
+                const float g = __ldg(p.grad_E);
+                p.out_grad[i] = make_float4(-g * pi.w * a.x, -g * pi.w * a.y, -g * pi.w * a.z, -g * (a.w - self));
+            }
+        }
+    }
+};
+
+// ---------------------------------------------------------------- energy
+struct EnergyParams {
+    const float4 *pos;
+    int64_t n;
+    float eps2;
+    double *out_E;
+    double *partial;     // one per work-group
+    unsigned *counter;   // work-groups finished in this run (reset by the last)
+    uint64_t G;
+    uint32_t lws;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct EnergyBody {
+    using Params = EnergyParams;
+    Params p;
+    float4 *sh;
+    double *dsh;  // [kBlock / 32] warp sums, then [1] flag
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
+    {
+        return one_chunk_per_wg(len);
+    }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const uint32_t lws = p.lws;
+        const uint32_t S = kBlock / lws;
+        const uint32_t b = threadIdx.x % lws, s = threadIdx.x / lws;
+        const uint64_t wg = off + t;
+        const int64_t i0 = (int64_t)wg * lws;
+        const int64_t i = i0 + b;
+        const bool valid = i < p.n;
+        const float4 pi = valid ? __ldg(p.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t span = kTile / S;
+        double e = 0.0;
+        const int64_t ntiles = (p.n + kTile - 1) / kTile;
+        // rows i < j only: tiles from the one holding this work-group onwards
+        for (int64_t tile = i0 / kTile; tile < ntiles; ++tile) {
+            __syncthreads();
+            stage_tile(sh, p.pos, p.n, tile);
+            __syncthreads();
+            float tp = 0.f;
+            const int64_t j0 = tile * kTile + s * span;
+            const float4 *q = sh + s * span;
+            if (j0 + (int64_t)span - 1 <= i) {
+                // whole slice at or before i: contributes nothing
+            } else if (j0 > i) {
+#pragma unroll 8
+                for (uint32_t k = 0; k < span; ++k) {
+                    const float4 pj = q[k];
+                    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2)));
+                    tp = fmaf(pj.w, rsqrtf(r2), tp);
+                }
+            } else {
+                for (uint32_t k = 0; k < span; ++k) {
+                    const float4 pj = q[k];
+                    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2)));
+                    const float m = (j0 + (int64_t)k > i) ? pj.w : 0.f;
+                    tp = fmaf(m, rsqrtf(r2), tp);
+                }
+            }
+            e += (double)tp;
+        }
+        // this thread's share of -m_i sum_{j>i} m_j phi_ij, reduced in a fixed order
+        double v = valid ? -(double)pi.w * e : 0.0;
+        v = warp_sum_d(v);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) dsh[threadIdx.x / 32] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double w = 0.0;
+            for (int q = 0; q < kBlock / 32; ++q) w += dsh[q];
+            p.partial[wg] = w;
+            __threadfence();
+            const unsigned before = atomicAdd(p.counter, 1u);
+            dsh[0] = (before + 1 == (unsigned)p.G) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        if (dsh[0] != 0.0) {  // last work-group of the run: sum the partials in order
+            __threadfence();
+            double acc = 0.0;
+            const uint64_t per = (p.G + kBlock - 1) / kBlock;
+            const uint64_t a = threadIdx.x * per;
+            const uint64_t z = min(p.G, a + per);
+            for (uint64_t w = a; w < z; ++w) acc += *((volatile double *)p.partial + w);
+            __syncthreads();
+            __shared__ double tree[kBlock];
+            tree[threadIdx.x] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int q = 0; q < kBlock; ++q) tot += tree[q];
+                *p.out_E = tot;
+                *p.counter = 0u;
+            }
+        }
+        __syncthreads();
+    }
+};
+
+// ---------------------------------------------------------------- finite differences
+struct FDParams {
+    const float4 *pos;
+    int64_t n;
+    float eps2, h;
+    const int *body, *comp;
+    int64_t count;
+    double *out;
+};
+
+struct FDBody {
+    using Params = FDParams;
+    Params p;
+    double *dsh;  // [2 * kBlock / 32]
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
+    {
+        return (uint32_t)len;
+    }
+
+    // chunk = one sample: -m_i * (row(q+) - row(q-)) / (x+ - x-),
+    // row(q) = sum_{j != i} m_j / sqrt(|q - r_j|^2 + eps2)
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const int64_t smp = (int64_t)(off + t);
+        if (smp >= p.count) return;
+        const int64_t i = p.body[smp];
+        const int c = p.comp[smp];
+        if (i < 0 || i >= p.n || c < 0 || c > 2) {  // invalid sample: NaN, no access
+            if (threadIdx.x == 0) p.out[smp] = __longlong_as_double(0x7ff8000000000000ll);
+            return;
+        }
+        const float4 pi = __ldg(p.pos + i);
+        const float xc = c == 0 ? pi.x : (c == 1 ? pi.y : pi.z);
+        const float xp = xc + p.h, xm = xc - p.h;
+        float4 qp = pi, qm = pi;
+        if (c == 0) { qp.x = xp; qm.x = xm; }
+        else if (c == 1) { qp.y = xp; qm.y = xm; }
+        else { qp.z = xp; qm.z = xm; }
+        double rp = 0.0, rm = 0.0;
+        for (int64_t j = threadIdx.x; j < p.n; j += kBlock) {
+            if (j == i) continue;
+            const float4 pj = __ldg(p.pos + j);
+            float dx = qp.x - pj.x, dy = qp.y - pj.y, dz = qp.z - pj.z;
+            const float fp = pj.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2))));
+            dx = qm.x - pj.x;
+            dy = qm.y - pj.y;
+            dz = qm.z - pj.z;
+            const float fm = pj.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2))));
+            rp += (double)fp;
+            rm += (double)fm;
+        }
+        rp = warp_sum_d(rp);
+        rm = warp_sum_d(rm);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            dsh[threadIdx.x / 32] = rp;
+            dsh[kBlock / 32 + threadIdx.x / 32] = rm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, z = 0.0;
+            for (int q = 0; q < kBlock / 32; ++q) {
+                a += dsh[q];
+                z += dsh[kBlock / 32 + q];
+            }
+            p.out[smp] = -(double)pi.w * (a - z) / ((double)xp - (double)xm);
+        }
+        __syncthreads();
+    }
+};
+
+// ---------------------------------------------------------------- kernels
+template <uint32_t MODE>
+__global__ void __launch_bounds__(kBlock) k_nbody_force(NBodyParams prm, SchedArgs s)
+{
+    __shared__ float4 sh[kTile];
+    __shared__ float4 red[kBlock];
+    ForceBody<MODE> b;
+    b.p = prm;
+    b.sh = sh;
+    b.red = red;
+    drive(s, b);
+}
+
+__global__ void __launch_bounds__(kBlock) k_nbody_energy(EnergyParams prm, SchedArgs s)
+{
+    __shared__ float4 sh[kTile];
+    __shared__ double dsh[kBlock / 32];
+    EnergyBody b;
+    b.p = prm;
+    b.sh = sh;
+    b.dsh = dsh;
+    drive(s, b);
+}
+
+__global__ void __launch_bounds__(kBlock) k_nbody_fd(FDParams prm, SchedArgs s)
+{
+    __shared__ double dsh[2 * kBlock / 32];
+    FDBody b;
+    b.p = prm;
+    b.dsh = dsh;
+    drive(s, b);
+}
+
+int occ(const void *fn)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+ecl_status launched(std::string &err)
+{
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
+}
+
+bool lws_ok(uint32_t lws) { return lws == 32 || lws == 64 || lws == 128 || lws == 256; }
+
+ecl_status check_bodies(const KArgs &a, int pos_arg, int n_arg, uint64_t gws, uint32_t lws, std::string &err)
+{
+    const int64_t n = a.i32(n_arg);
+    if (n <= 0) {
+        err = "bodies must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (!lws_ok(lws)) {
+        err = "lws must be 32, 64, 128 or 256";
+        return ECL_ERR_SIZE;
+    }
+    if (gws < (uint64_t)n) {
+        err = "the NDRange (one body per work-item) does not cover the bodies";
+        return ECL_ERR_SIZE;
+    }
+    if (a.bytes[pos_arg] < (uint64_t)n * 16 || (uintptr_t)a.ptr[pos_arg] % 16) {
+        err = "positions must be 16-byte aligned float4[n]";
+        return ECL_ERR_BUFFER;
+    }
+    return ECL_OK;
+}
+
+bool out4_ok(const KArgs &a, int i, int64_t n) { return a.bytes[i] >= (uint64_t)n * 16 && (uintptr_t)a.ptr[i] % 16 == 0; }
+
+uint64_t grain1(const KArgs &, uint64_t, uint32_t) { return 1; }
+
+uint32_t nchunks_wg(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+// ---- nbody (Listing 2 order): in_pos, in_vel, bodies, del_t, esp_sqr, out_pos, out_vel
+ecl_status v_step(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    ecl_status st = check_bodies(a, 0, 2, gws, lws, err);
+    if (st != ECL_OK) return st;
+    const int64_t n = a.i32(2);
+    if (!out4_ok(a, 1, n) || !out4_ok(a, 5, n) || !out4_ok(a, 6, n)) {
+        err = "velocity and output buffers must be 16-byte aligned float4[n]";
+        return ECL_ERR_BUFFER;
+    }
+    return ECL_OK;
+}
+
+ecl_status l_step(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    NBodyParams p{};
+    p.pos = a.buf<const float4>(0);
+    p.vel = a.buf<const float4>(1);
+    p.n = a.i32(2);
+    p.dt = a.f32(3);
+    p.eps2 = a.f32(4);
+    p.out_pos = a.buf<float4>(5);
+    p.out_vel = a.buf<float4>(6);
+    p.lws = c.lws;
+    k_nbody_force<NB_STEP><<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    return launched(err);
+}
+
+int o_step() { return occ((const void *)k_nbody_force<NB_STEP>); }
+
+// ---- nbody_acc: in_pos, bodies, esp_sqr, out_acc
+ecl_status v_acc(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    ecl_status st = check_bodies(a, 0, 1, gws, lws, err);
+    if (st != ECL_OK) return st;
+    if (!out4_ok(a, 3, a.i32(1))) {
+        err = "out_acc must be a 16-byte aligned float4[n]";
+        return ECL_ERR_BUFFER;
+    }
+    return ECL_OK;
+}
+
+ecl_status l_acc(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    NBodyParams p{};
+    p.pos = a.buf<const float4>(0);
+    p.n = a.i32(1);
+    p.eps2 = a.f32(2);
+    p.out_acc = a.buf<float4>(3);
+    p.lws = c.lws;
+    k_nbody_force<NB_ACC><<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    return launched(err);
+}
+
+int o_acc() { return occ((const void *)k_nbody_force<NB_ACC>); }
+
+// ---- nbody_adjoint: in_pos, bodies, esp_sqr, grad_E, out_grad
+ecl_status v_adj(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    ecl_status st = check_bodies(a, 0, 1, gws, lws, err);
+    if (st != ECL_OK) return st;
+    if (a.bytes[3] < 4) {
+        err = "grad_E must hold one float";
+        return ECL_ERR_BUFFER;
+    }
+    if (!out4_ok(a, 4, a.i32(1))) {
+        err = "out_grad must be a 16-byte aligned float4[n]";
+        return ECL_ERR_BUFFER;
+    }
+    return ECL_OK;
+}
+
+ecl_status l_adj(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    NBodyParams p{};
+    p.pos = a.buf<const float4>(0);
+    p.n = a.i32(1);
+    p.eps2 = a.f32(2);
+    p.grad_E = a.buf<const float>(3);
+    p.out_grad = a.buf<float4>(4);
+    p.lws = c.lws;
+    k_nbody_force<NB_ADJ><<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    return launched(err);
+}
+
+int o_adj() { return occ((const void *)k_nbody_force<NB_ADJ>); }
+
+// ---- nbody_energy: in_pos, bodies, esp_sqr, out_energy (double[1]); workspace: G partials + counter
+ecl_status v_energy(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    ecl_status st = check_bodies(a, 0, 1, gws, lws, err);
+    if (st != ECL_OK) return st;
+    if (a.bytes[3] < 8 || (uintptr_t)a.ptr[3] % 8) {
+        err = "out_energy must be an aligned double[1]";
+        return ECL_ERR_BUFFER;
+    }
+    if (gws / lws > 0xffffffffull) {
+        err = "too many work-groups";
+        return ECL_ERR_SIZE;
+    }
+    return ECL_OK;
+}
+
+ecl_status l_energy(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    const uint64_t G = c.gws / c.lws;
+    char *ws = (char *)workspace_get(c.ws, 256 + G * sizeof(double), err);
+    if (!ws) return ECL_ERR_CUDA;
+    EnergyParams p{};
+    p.pos = a.buf<const float4>(0);
+    p.n = a.i32(1);
+    p.eps2 = a.f32(2);
+    p.out_E = a.buf<double>(3);
+    p.counter = (unsigned *)ws;
+    p.partial = (double *)(ws + 256);
+    p.G = G;
+    p.lws = c.lws;
+    k_nbody_energy<<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    return launched(err);
+}
+
+int o_energy() { return occ((const void *)k_nbody_energy); }
+
+// ---- nbody_fd: in_pos, bodies, esp_sqr, h, body[], comp[], count, out[] (double)
+ecl_status v_fd(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    const int64_t n = a.i32(1), cnt = a.i32(6);
+    if (n <= 0 || cnt <= 0) {
+        err = "bodies and sample count must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (lws != 1 || gws < (uint64_t)cnt) {
+        err = "one work-group (lws 1) per sample";
+        return ECL_ERR_SIZE;
+    }
+    if (a.bytes[0] < (uint64_t)n * 16 || (uintptr_t)a.ptr[0] % 16) {
+        err = "positions must be 16-byte aligned float4[n]";
+        return ECL_ERR_BUFFER;
+    }
+    if (a.bytes[4] < (uint64_t)cnt * 4 || a.bytes[5] < (uint64_t)cnt * 4 || a.bytes[7] < (uint64_t)cnt * 8) {
+        err = "sample buffers smaller than the sample count";
+        return ECL_ERR_BUFFER;
+    }
+    return ECL_OK;
+}
+
+ecl_status l_fd(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    FDParams p{};
+    p.pos = a.buf<const float4>(0);
+    p.n = a.i32(1);
+    p.eps2 = a.f32(2);
+    p.h = a.f32(3);
+    p.body = a.buf<const int>(4);
+    p.comp = a.buf<const int>(5);
+    p.count = a.i32(6);
+    p.out = a.buf<double>(7);
+    k_nbody_fd<<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    return launched(err);
+}
+
+int o_fd() { return occ((const void *)k_nbody_fd); }
+
+}  // namespace
+
+extern const KernelDesc kNBody = {
+    "nbody", 7,
+    {{"in_pos", A_BUF_IN}, {"in_vel", A_BUF_IN}, {"bodies", A_I32}, {"del_t", A_F32}, {"esp_sqr", A_F32},
+     {"out_pos", A_BUF_OUT}, {"out_vel", A_BUF_OUT}},
+    1, 1, kBlock, 0, v_step, grain1, nchunks_wg, o_step, l_step,
+};
+
+extern const KernelDesc kNBodyAcc = {
+    "nbody_acc", 4,
+    {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_acc", A_BUF_OUT}},
+    1, 1, kBlock, 0, v_acc, grain1, nchunks_wg, o_acc, l_acc,
+};
+
+extern const KernelDesc kNBodyAdjoint = {
+    "nbody_adjoint", 5,
+    {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"grad_E", A_BUF_IN},
+     {"out_grad", A_BUF_OUT}},
+    1, 1, kBlock, 0, v_adj, grain1, nchunks_wg, o_adj, l_adj,
+};
+
+extern const KernelDesc kNBodyEnergy = {
+    "nbody_energy", 4,
+    {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_energy", A_BUF_OUT}},
+    1, 0, kBlock, 0, v_energy, grain1, nchunks_wg, o_energy, l_energy,
+};
+
+extern const KernelDesc kNBodyFD = {
+    "nbody_fd", 8,
+    {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"h", A_F32}, {"body", A_BUF_IN},
+     {"comp", A_BUF_IN}, {"count", A_I32}, {"out", A_BUF_OUT}},
+    1, 1, kBlock, 0, v_fd, grain1, nchunks_wg, o_fd, l_fd,
+};
+
+}  // namespace ecl

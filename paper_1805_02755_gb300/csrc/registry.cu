@@ -8,10 +8,22 @@ namespace ecl {
 
 extern const KernelDesc kMandelbrot;
 extern const KernelDesc kGaussian;
+extern const KernelDesc kNBody;
+extern const KernelDesc kNBodyAcc;
+extern const KernelDesc kNBodyAdjoint;
+extern const KernelDesc kNBodyEnergy;
+extern const KernelDesc kNBodyFD;
+extern const KernelDesc kBinomial;
 
 static const KernelDesc *const kAll[] = {
     &kMandelbrot,
     &kGaussian,
+    &kNBody,
+    &kNBodyAcc,
+    &kNBodyAdjoint,
+    &kNBodyEnergy,
+    &kNBodyFD,
+    &kBinomial,
 };
 
 const KernelDesc *find_kernel(const char *name)

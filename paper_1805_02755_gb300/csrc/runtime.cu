@@ -37,6 +37,13 @@ void *workspace_get(Workspace *ws, size_t bytes, std::string &err)
         ws->ptr = nullptr;
         return nullptr;
     }
+    ce = cudaMemset(ws->ptr, 0, bytes);  // kernels rely on zeroed counters
+    if (ce != cudaSuccess) {
+        err = std::string("cudaMemset(workspace): ") + cudaGetErrorString(ce);
+        cudaFree(ws->ptr);
+        ws->ptr = nullptr;
+        return nullptr;
+    }
     ws->bytes = bytes;
     return ws->ptr;
 }
@@ -80,7 +87,7 @@ struct ecl_engine {
     int D = 0, C = 0;
     int sms = 0;
     // errors
-    std::string first_error;
+    std::string last_error;
     int nerrors = 0;
     // device memory
     Queue *q = nullptr;
@@ -120,7 +127,7 @@ ecl_status fail(ecl_engine *e, ecl_status st, const char *fmt, ...)
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
     if (e) {
-        if (e->nerrors == 0) e->first_error = buf;
+        e->last_error = buf;
         e->nerrors++;
     }
     return st;
@@ -310,6 +317,7 @@ ecl_status check_device_error(ecl_engine *e)
         // the run is void: put the queue back in its initial state
         CUDA_OR_FAIL(e, cudaMemsetAsync(e->q, 0, sizeof(Queue), e->stream));
         if (e->dev) CUDA_OR_FAIL(e, cudaMemsetAsync(e->dev, 0, e->dev_cap * sizeof(DevState), e->stream));
+        if (e->ws.ptr) CUDA_OR_FAIL(e, cudaMemsetAsync(e->ws.ptr, 0, e->ws.bytes, e->stream));
         CUDA_OR_FAIL(e, cudaStreamSynchronize(e->stream));
         return fail(e, ECL_ERR_TIMEOUT, "device wait gave up (CTA %llu after %llu polls); the run is void",
                     info >> 32, info & 0xffffffffull);
@@ -437,7 +445,7 @@ ecl_status ecl_set_coverage(ecl_engine *e, uint32_t *counts, uint64_t n)
 const char *ecl_last_error(const ecl_engine *e)
 {
     if (!e) return "NULL engine";
-    return e->first_error.c_str();
+    return e->last_error.c_str();
 }
 
 int ecl_error_count(const ecl_engine *e) { return e ? e->nerrors : 0; }
@@ -446,7 +454,7 @@ void ecl_clear_errors(ecl_engine *e)
 {
     if (!e) return;
     e->nerrors = 0;
-    e->first_error.clear();
+    e->last_error.clear();
 }
 
 ecl_status ecl_plan_info(const ecl_engine *e, uint64_t *G, uint64_t *packages, uint32_t *devices,

@@ -11,7 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-KERNELS = ["mandelbrot", "gaussian"]
+KERNELS = ["mandelbrot", "gaussian", "nbody", "nbody_acc", "nbody_adjoint", "nbody_energy", "nbody_fd", "binomial"]
 
 
 @pytest.fixture(scope="module")

@@ -1,0 +1,110 @@
+"""Binomial (CRR European call) through the C ABI vs the FP64 oracle.
+
+Tolerance from the FP32 error analysis of the lattice: each backward level adds
+at most eps times the probability-weighted node values, whose sum is the price
+itself, so the error is ~sqrt(N) eps V (N eps V worst case); 1e-5 relative is
+applied to max(V64, 1e-4 S) so that prices far out of the money, which carry
+the rounding of S-sized leaves, are judged on the scale of S.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1805_02755_gb300 import build as B
+    B.build()
+    import paper_1805_02755_gb300 as E
+    return E
+
+
+def run_bino(E, o, greeks=True, sched="hguided", params=(2.0, 1.0), D=8, C=0, coverage=False):
+    import torch
+    n = len(o["S"])
+    t = {k: torch.from_numpy(np.ascontiguousarray(o[k])).cuda() for k in ("S", "K", "T", "sigma", "steps")}
+    price = torch.full((n,), -1.0, device="cuda")
+    gr = torch.full((n, 2), -1.0, device="cuda") if greeks else None
+    eng = E.Engine(0)
+    cov = torch.zeros(n, dtype=torch.int32, device="cuda") if coverage else None
+    p = E.Program("binomial")
+    for k in ("S", "K", "T", "sigma", "steps"):
+        p.in_(t[k])
+    p.out(price)
+    if gr is not None:
+        p.out(gr)
+    p.args(t["S"], t["K"], t["T"], t["sigma"], t["steps"], o["r"], n, price, gr)
+    eng.work_items(n * 32, 32).scheduler(sched, params).workers(D, C).program(p)
+    eng.set_coverage(cov)
+    eng.run().synchronize()
+    out = (price.cpu().numpy(), gr.cpu().numpy() if gr is not None else None, cov)
+    eng.close()
+    return out
+
+
+def check(o, price, gr, oracle_mod, idx=None):
+    idx = np.arange(len(o["S"])) if idx is None else idx
+    sub = {k: o[k][idx] for k in ("S", "K", "T", "sigma", "steps")}
+    rp, rd, rv = oracle_mod.binomial(sub["S"], sub["K"], sub["T"], sub["sigma"], sub["steps"], o["r"])
+    S = sub["S"].astype(np.float64)
+    ep = np.abs(price[idx] - rp) / np.maximum(rp, 1e-4 * S)
+    assert ep.max() <= RTOL, (ep.max(), idx[ep.argmax()])
+    if gr is not None:
+        ed = np.abs(gr[idx, 0] - rd) / np.maximum(np.abs(rd), 1e-4)
+        ev = np.abs(gr[idx, 1] - rv) / np.maximum(np.abs(rv), 1e-4 * S)
+        assert ed.max() <= RTOL, (ed.max(), idx[ed.argmax()])
+        assert ev.max() <= RTOL, (ev.max(), idx[ev.argmax()])
+    return ep.max()
+
+
+@pytest.mark.parametrize("lo,hi", [(1, 40), (1, 300), (256, 700), (1000, 2048)])
+def test_depth_ranges(E, oracle_mod, lo, hi):
+    o = W.binomial_options(300 if hi < 1000 else 60, seed=400 + lo, min_steps=lo, max_steps=hi)
+    price, gr, _ = run_bino(E, o)
+    check(o, price, gr, oracle_mod)
+
+
+def test_every_depth_boundary(E, oracle_mod):
+    # depths at every register-blocking switch (32, 64, ..., 1024) and the extremes
+    steps = np.array([1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1023,
+                      1024, 1025, 2047, 2048], dtype=np.int32)
+    o = W.binomial_options(len(steps), seed=41)
+    o["steps"] = steps
+    price, gr, _ = run_bino(E, o)
+    check(o, price, gr, oracle_mod)
+
+
+def test_price_only_equals_price_with_greeks(E):
+    o = W.binomial_options(500, seed=42)
+    p1, _, _ = run_bino(E, o, greeks=False)
+    p2, _, _ = run_bino(E, o, greeks=True)
+    assert np.array_equal(p1, p2)
+
+
+@pytest.mark.parametrize("sched,params,D,C", [("static", (), 1, 0), ("dynamic", (64,), 0, 0),
+                                              ("hguided", (2.0, 1.0), 0, 0), ("monolithic", (), 0, 0)])
+def test_schedulers(E, oracle_mod, sched, params, D, C):
+    o = W.binomial_options(400, seed=43, min_steps=1, max_steps=600)
+    price, gr, cov = run_bino(E, o, True, sched, params, D, C, coverage=(sched != "monolithic"))
+    check(o, price, gr, oracle_mod)
+    if cov is not None:
+        assert (cov.cpu().numpy() == 1).all()
+
+
+def test_config4_full_batch_sampled(E, oracle_mod):
+    o = W.binomial_options(1 << 20)
+    price, gr, _ = run_bino(E, o, True, "hguided", (2.0, 1.0), 8, 0)
+    assert np.isfinite(price).all() and np.isfinite(gr).all()
+    idx = np.sort(np.random.default_rng(7).choice(1 << 20, 384, replace=False))
+    check(o, price, gr, oracle_mod, idx)
+    # price within no-arbitrage bounds everywhere: max(S - K e^{-rT}, 0) <= C <= S
+    S, K, T = o["S"], o["K"], o["T"]
+    lb = np.maximum(S - K * np.exp(-o["r"] * T), 0)
+    assert (price >= lb - 1e-4 * S).all() and (price <= S * (1 + 1e-6)).all()
+    assert (gr[:, 0] >= -1e-6).all() and (gr[:, 0] <= 1 + 1e-5).all() and (gr[:, 1] >= -1e-4).all()

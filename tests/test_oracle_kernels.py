@@ -185,6 +185,22 @@ def test_nbody_energy_gradient_finite_difference(oracle_mod):
     assert np.allclose(fd, ref, rtol=2e-3, atol=1e-3 * np.abs(g).max())
 
 
+def test_nbody_potential_pins(oracle_mod):
+    pos, _ = W.nbody_bodies(120, seed=15)
+    eps2 = 1e-3
+    phi = oracle_mod.nbody_potential(pos, eps2)
+    m = pos[:, 3].astype(np.float64)
+    E = oracle_mod.nbody_energy(pos, eps2)
+    # every pair appears twice in sum_i m_i phi_i
+    assert math.isclose((m * phi).sum(), -2.0 * E, rel_tol=1e-12)
+    # dE/dm_i = -phi_i: E is linear in m_i, so a finite difference in the mass is exact
+    i = 17
+    q = pos.copy()
+    q[i, 3] = np.float32(pos[i, 3] + np.float32(0.25))
+    dm = float(q[i, 3]) - float(pos[i, 3])
+    assert math.isclose((oracle_mod.nbody_energy(q, eps2) - E) / dm, -phi[i], rel_tol=1e-9)
+
+
 def test_nbody_step_kinematics(oracle_mod):
     pos, vel = W.nbody_bodies(50, seed=14)
     vel[:, :3] = 0.1
