@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
+SMALL = False  # --small: reduced sizes for profiler captures (never a bench value)
 METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
 L2_FLUSH_BYTES = 512 << 20
 SMS_NOMINAL = 152
@@ -85,6 +86,16 @@ class Workload:
     def work_items(self):
         return self.gws
 
+    def programs(self):
+        """(name, engine, work-items) of every program the step runs."""
+        if isinstance(self.eng, MultiEngine):
+            return list(zip(self.eng.names, self.eng.engs, self.eng.wis))
+        return [(self.name, self.eng, self.gws)]
+
+    def alg(self, name):
+        """Algorithmic work of one program: bound, flops and/or bytes, own unit."""
+        return self.after()
+
 
 class Mandelbrot(Workload):
     name = "mandelbrot"
@@ -130,7 +141,7 @@ class Gaussian(Workload):
     sched = ("dynamic", (256,), 8, 0)  # 256 row packages over 8 devices of CTAs
 
     def host_setup(self):
-        self.H = self.Wd = 8192
+        self.H = self.Wd = 6144 if SMALL else 8192
         self.img = W.gaussian_image(self.H, self.Wd)
         self.w = W.gaussian_weights(31, 5.0)
         self.lws = 128
@@ -171,7 +182,7 @@ class NBody(Workload):
     NFD = 256
 
     def host_setup(self):
-        self.n = 65536
+        self.n = 16384 if SMALL else 65536
         self.pos, _ = W.nbody_bodies(self.n)
         self.lws = 64
         self.gws = self.n
@@ -213,11 +224,18 @@ class NBody(Workload):
     def work_items(self):
         return 3 * self.n + self.NFD
 
-    def after(self):
+    def alg(self, name):
         n = self.n
-        # FP32 flops per pair (FMA = 2): force 18, energy (i<j) 11, adjoint 20
-        flops = 18.0 * n * n + 11.0 * n * (n - 1) / 2 + 20.0 * n * n
-        return dict(bound="alu", flops=flops, unit_name="interactions/s", units=2 * n * n + n * (n - 1) // 2)
+        # FP32 flops per pair, FMA counted as 2: force 18 (3 sub, 3 FMA, 3 mul, 3 FMA),
+        # energy 10 over i<j (3 sub, 3 FMA, 1 FMA), adjoint 19 (force + potential add),
+        # finite differences 2 x 9 per j for each sample
+        if name == "nbody_acc":
+            return dict(bound="alu", flops=18.0 * n * n, unit_name="interactions/s", units=n * n)
+        if name == "nbody_energy":
+            return dict(bound="alu", flops=10.0 * n * (n - 1) / 2, unit_name="pairs/s", units=n * (n - 1) // 2)
+        if name == "nbody_adjoint":
+            return dict(bound="alu", flops=19.0 * n * n, unit_name="interactions/s", units=n * n)
+        return dict(bound="alu", flops=18.0 * n * self.NFD, unit_name="samples/s", units=self.NFD)
 
     def cpu_sample(self, O, threads):
         t = time.perf_counter()
@@ -235,7 +253,7 @@ class Binomial(Workload):
     sched = ("hguided", (2.0, 1.0), 8, 0)
 
     def host_setup(self):
-        self.n = 1 << 20
+        self.n = (1 << 14) if SMALL else (1 << 20)
         self.o = W.binomial_options(self.n)
         self.lws = 32
         self.gws = self.n * 32
@@ -286,11 +304,82 @@ class Binomial(Workload):
         return k / self.n, time.perf_counter() - t, "%d of %d options (price, delta, vega)" % (k, self.n)
 
 
+class Gemm(Workload):
+    """Config 5: M = N = K = 8192, HGuided packages of 128-row tiles over 4
+    devices; the plain BF16 product and the split-BF16 three-product mode."""
+    name = "gemm"
+    sched = ("hguided", (2.0, 1.0), 4, 0)
+    M = N = K = 8192
+
+    def host_setup(self):
+        if SMALL:
+            self.M = self.N = self.K = 4096
+        self.A, self.Bt = W.gemm_matrices(self.M, self.N, self.K)
+        self.lws = 128 * 256
+        self.tiles = (self.M // 128) * (self.N // 256)
+        self.gws = self.tiles * self.lws
+
+    def setup(self):
+        torch = self.torch
+        E = self.E
+        self.host_setup()
+        A, Bt = torch.from_numpy(self.A), torch.from_numpy(self.Bt)
+        dA, dB = A.cuda(), Bt.cuda()
+        ab = torch.empty(self.A.shape, dtype=torch.bfloat16, device="cuda")
+        bb = torch.empty(self.Bt.shape, dtype=torch.bfloat16, device="cuda")
+        for src, dst in ((dA, ab), (dB, bb)):  # the input cast, in the library's kernel
+            ce = E.Engine(0)
+            pr = E.Program("cast_bf16").in_(src).out(dst).args(src, dst, src.numel())
+            ce.work_items(src.numel(), 256).scheduler("dynamic", (256,)).program(pr).run().synchronize()
+            ce.close()
+        self.d_in = [ab, bb, dA, dB]
+        self.d_out = [torch.zeros(self.M * self.N, device="cuda"), torch.zeros(self.M * self.N, device="cuda")]
+        self.h_in = [ab.cpu().pin_memory(), bb.cpu().pin_memory(), A.pin_memory(), Bt.pin_memory()]
+        self.h_out = [torch.zeros(self.M * self.N).pin_memory(), torch.zeros(self.M * self.N).pin_memory()]
+        del dA, dB
+        self.config = dict(M=self.M, N=self.N, K=self.K, tile="128x256x64", scheduler="hguided k=2 over 4 devices",
+                           programs="gemm_bf16 (bf16 inputs) + gemm_split3 (fp32 inputs, 3 products)")
+
+    def make_engine(self, sched, params, D=0, C=0, host=False):
+        E = self.E
+        ins, outs = (self.h_in, self.h_out) if host else (self.d_in, self.d_out)
+        ab, bb, af, bf = ins
+        c1, c2 = outs
+        progs = [
+            (E.Program("gemm_bf16").in_(ab).in_(bb).out(c1).args(ab, bb, c1, self.M, self.N, self.K),
+             self.gws, self.lws),
+            (E.Program("gemm_split3").in_(af).in_(bf).out(c2).args(af, bf, c2, self.M, self.N, self.K),
+             self.gws, self.lws),
+        ]
+        return MultiEngine(E, progs, sched, params, D, C)
+
+    def work_items(self):
+        return 2 * self.M * self.N
+
+    def alg(self, name):
+        f = 2.0 * self.M * self.N * self.K
+        if name == "gemm_bf16":
+            return dict(bound="tensor", flops=f, unit_name="TFLOP/s", units=f / 1e12)
+        # three products on the tensor cores (+ the split pass); "effective" counts the plain product
+        return dict(bound="tensor", flops=3.0 * f, unit_name="effective TFLOP/s", units=f / 1e12)
+
+    def cpu_sample(self, O, threads):
+        rng = W.rng(5)
+        ii = rng.integers(0, self.M, 64)
+        jj = rng.integers(0, self.N, 64)
+        t = time.perf_counter()
+        O.gemm_entries(self.A, self.Bt, 0, ii, jj, threads=threads)
+        O.gemm_entries(self.A, self.Bt, 2, ii, jj, threads=threads)
+        return 64 / (self.M * self.N), time.perf_counter() - t, "64 of %d entries, both modes" % (self.M * self.N)
+
+
 class MultiEngine:
     """Several programs of one configuration, each on its own engine, run in order."""
 
     def __init__(self, E, progs, sched, params, D, C):
         self.engs = []
+        self.names = [pr.kernel for pr, _, _ in progs]
+        self.wis = [g for _, g, _ in progs]
         for prog, gws, lws in progs:
             e = E.Engine(0)
             e.work_items(gws, lws).scheduler(sched, params).workers(D if lws > 1 else 0, C if lws > 1 else 0)
@@ -320,7 +409,7 @@ class MultiEngine:
         return len(self.engs)
 
 
-WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial]
+WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial, Gemm]
 
 
 # ====================================================================== helpers
@@ -416,12 +505,14 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    progs = [(w, name, eng, wi) for w in wls for (name, eng, wi) in w.programs()]
+
     def step(record):
         flush.fill_(1.0)  # evict L2 (outside the timed events)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(wls) + 1)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(progs) + 1)]
         ev[0].record(stream)
-        for i, w in enumerate(wls):
-            w.eng.run()
+        for i, (_, _, eng, _) in enumerate(progs):
+            eng.run()
             ev[i + 1].record(stream)
         record.append(ev)
 
@@ -440,18 +531,18 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    per = {w.name: [] for w in wls}
+    per = {name: [] for _, name, _, _ in progs}
     tot = []
     for ev in recs:
         tot.append(ev[0].elapsed_time(ev[-1]))
-        for i, w in enumerate(wls):
-            per[w.name].append(ev[i].elapsed_time(ev[i + 1]))
+        for i, (_, name, _, _) in enumerate(progs):
+            per[name].append(ev[i].elapsed_time(ev[i + 1]))
     step_ms = sum(tot) / len(tot)
     if world > 1:
         t = torch.tensor([step_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_ms = float(t.item())
-    launches = sum(getattr(w.eng, "launches", 1) for w in wls)  # one persistent launch per program
+    launches = sum(2 if name == "gemm_split3" else 1 for _, name, _, _ in progs)  # split pass + main loop
 
     # scheduler overhead against the monolithic launch (same kernel body, no queue)
     def timed(fn, n):
@@ -469,17 +560,22 @@ def run_ours(args):
 
     kern = {}
     dominant = None
+    monos = {}
     for w in wls:
-        ms = statistics.median(per[w.name])
-        ms_mono = timed(w.mono.run, max(5, args.steps))
-        ms_sched = timed(w.eng.run, max(5, args.steps))
-        alg = w.after()
-        st = w.eng.stats()
-        wst = w.eng.worker_stats()
-        info = w.eng.plan_info()
-        d = dict(ms=ms, work_items=w.work_items(), work_items_per_s=w.work_items() / (ms * 1e-3),
-                 config=w.config, plan=info, overhead_vs_monolithic_pct=100.0 * (ms_sched - ms_mono) / ms_mono,
-                 ms_monolithic=ms_mono, ms_scheduled_isolated=ms_sched,
+        for name, eng, _ in (zip(w.mono.names, w.mono.engs, w.mono.wis) if isinstance(w.mono, MultiEngine)
+                             else [(w.name, w.mono, 0)]):
+            monos[name] = eng
+    for w, name, eng, wi in progs:
+        ms = statistics.median(per[name])
+        ms_mono = timed(monos[name].run, max(5, min(args.steps, 10)))
+        ms_sched = timed(eng.run, max(5, min(args.steps, 10)))
+        alg = w.alg(name)
+        st = eng.stats()
+        wst = eng.worker_stats()
+        info = eng.plan_info()
+        d = dict(ms=ms, work_items=wi, work_items_per_s=wi / (ms * 1e-3),
+                 overhead_vs_monolithic_pct=100.0 * (ms_sched - ms_mono) / ms_mono,
+                 ms_monolithic=ms_mono, ms_scheduled_isolated=ms_sched, plan=info,
                  balance_T_FD_over_T_LD=balance_of(st), cta_busy_efficiency=worker_efficiency(wst),
                  packages=len(st))
         d[alg["unit_name"]] = alg["units"] / (ms * 1e-3)
@@ -506,9 +602,11 @@ def run_ours(args):
             ach = alg["flops"] / (ms * 1e-3) / 1e12
             pk = peaks["bf16_tflops"]
             d["roofline"] = dict(bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk)
-        kern[w.name] = d
+        kern[name] = d
         if dominant is None or ms > kern[dominant]["ms"]:
-            dominant = w.name
+            dominant = name
+    if "gemm_bf16" in kern and "gemm_split3" in kern:
+        kern["gemm_split3"]["compensated_over_plain"] = kern["gemm_split3"]["ms"] / kern["gemm_bf16"]["ms"]
 
     # end to end through host (pinned) buffers: the engine copies in, runs, copies out
     h2d = sum(t.numel() * t.element_size() for w in wls for t in w.h_in)
@@ -523,7 +621,7 @@ def run_ours(args):
             w.host.run()
     e2e_s = (time.perf_counter() - t0) / args.steps
 
-    total_wi = sum(w.work_items() for w in wls)
+    total_wi = sum(wi for _, _, _, wi in progs)
     value = total_wi * world / (step_ms * 1e-3)
     rf = dict(kern[dominant]["roofline"])
     rf["kernel"] = dominant
@@ -619,7 +717,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--only", default="")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="reduced sizes for profiler captures")
     args = ap.parse_args()
+    global SMALL
+    SMALL = args.small
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

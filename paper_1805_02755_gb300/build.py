@@ -27,6 +27,7 @@ SOURCES = {
     "k_gaussian.cu": [],
     "k_nbody.cu": [],
     "k_binomial.cu": [],
+    "k_gemm.cu": [],
 }
 HEADERS = ["ecl_internal.h", "sched.cuh"]
 

@@ -18,6 +18,12 @@
 // update is  B_j <- (B_{j+1} + B_j) + 2q (B_{j+1} - B_j)  (add, sub, FMA);
 // every 32 levels all nodes are multiplied by 2^-32 (exact) and the power
 // is removed at the end together with disc^N = e^{-rT}.
+// In-the-money calls (S > K) are priced through the put on the same lattice
+// and put-call parity, which holds exactly on a CRR lattice:
+//   C = P + S - K e^{-rT},  dC/dS = dP/dS + 1,  dC/dsigma = dP/dsigma.
+// The put lattice of a deep in-the-money call holds small values, while the
+// call lattice would carry two large vega terms (leaf and dq/dsigma parts)
+// that cancel, losing several digits in FP32.
 // Greeks are the exact derivatives of this discrete price (forward mode):
 //   delta tree: same recursion, leaves u^j d^(N-j) for in-the-money leaves;
 //   vega tree:  dB_j <- (dB_{j+1} + dB_j) + 2q (dB_{j+1} - dB_j) + 2q' (B_{j+1} - B_j),
@@ -142,6 +148,7 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o)
     L.active = N;  // nodes of level N-1
     L.rescale = 0;
     L.shift = N;
+    const bool put = S > K;  // price the out-of-the-money side, then parity
     float B[R], D[R], V[R];
     // level N-1 directly from the leaves j and j+1
     float lb = 0.f, ld = 0.f, lv = 0.f;  // leaf j of the previous slot (j+1 of this one)
@@ -153,11 +160,11 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o)
             const float m = (float)(2 * j - N);
             const float g = expf(a * m);
             const float ST = S * g;
-            if (ST > K) {
-                b = ST - K;
+            if (put ? (ST < K) : (ST > K)) {
+                b = put ? K - ST : ST - K;
                 if (G) {
-                    d = g;
-                    v = ST * m * sdt;
+                    d = put ? -g : g;
+                    v = put ? -(ST * m * sdt) : ST * m * sdt;
                 }
             }
         }
@@ -179,8 +186,13 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o)
         // remove the remaining 2^shift (exact), then discount
         const float disc = expf(-p.r * T);
         const float scale = ldexpf(disc, -L.shift);
-        p.price[o] = B[0] * scale;
-        if (G) p.greeks[o] = make_float2(D[0] * scale, V[0] * scale);
+        float price = B[0] * scale, delta = D[0] * scale;
+        if (put) {
+            price += S - K * disc;
+            delta += 1.0f;
+        }
+        p.price[o] = price;
+        if (G) p.greeks[o] = make_float2(delta, V[0] * scale);
     }
 }
 

@@ -14,6 +14,9 @@ extern const KernelDesc kNBodyAdjoint;
 extern const KernelDesc kNBodyEnergy;
 extern const KernelDesc kNBodyFD;
 extern const KernelDesc kBinomial;
+extern const KernelDesc kGemmBF16;
+extern const KernelDesc kGemmSplit3;
+extern const KernelDesc kCastBF16;
 
 static const KernelDesc *const kAll[] = {
     &kMandelbrot,
@@ -24,6 +27,9 @@ static const KernelDesc *const kAll[] = {
     &kNBodyEnergy,
     &kNBodyFD,
     &kBinomial,
+    &kGemmBF16,
+    &kGemmSplit3,
+    &kCastBF16,
 };
 
 const KernelDesc *find_kernel(const char *name)

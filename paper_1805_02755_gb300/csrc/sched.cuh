@@ -180,6 +180,56 @@ __device__ Claim claim_chunks(const SchedArgs &s, const typename Body::Params &b
     }
 }
 
+// Chunk accounting after a CTA finished chunks [t_begin, t_end) of c.pkg:
+// returns true when this completed the package (then t1 is stamped).
+__device__ __forceinline__ bool finish_chunks(const SchedArgs &s, uint32_t pkg, uint32_t n, uint32_t nchunks,
+                                              uint64_t te)
+{
+    const uint32_t prev = (s.C == 1) ? 0u : atomicAdd(&s.rec[pkg].done, n);
+    const bool finished = (prev + n == nchunks);
+    if (finished) {
+        s.rec[pkg].t1 = te;
+        s.rec[pkg].done = nchunks;
+    }
+    return finished;
+}
+
+// End of a persistent CTA (all threads call it): writes the per-CTA record,
+// and the last CTA to leave puts the queue back to its initial state.
+__device__ __forceinline__ void exit_protocol(const SchedArgs &s, uint32_t d, uint64_t t_first, uint64_t t_last,
+                                              uint64_t busy, uint32_t nchunks_done, uint32_t *flag)
+{
+    if (threadIdx.x == 0) {
+        ecl_worker_stat w;
+        w.t_first_ns = t_first;
+        w.t_last_ns = t_last;
+        w.busy_ns = busy;
+        w.cta = blockIdx.x;
+        w.device = d;
+        w.smid = smid();
+        w.chunks = nchunks_done;
+        s.wst[blockIdx.x] = w;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&s.q->exit_count, 1u);
+        *flag = (ticket == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (*flag) {
+        __threadfence();
+        for (uint32_t i = threadIdx.x; i < s.D; i += blockDim.x) {
+            s.dev[i].word = 0ull;
+            s.dev[i].fetches = 0u;
+        }
+        if (threadIdx.x == 0) {
+            s.q->last_npkg = s.q->cursor;
+            s.q->cursor = 0ull;
+            s.q->consumed = 0ull;
+            s.q->exit_count = 0u;
+        }
+        __threadfence();
+    }
+}
+
 // The persistent driver.  Body must provide
 //   struct Params;                                   (kernel arguments)
 //   static __host__ __device__ uint32_t nchunks(const Params&, off, len);
@@ -212,12 +262,7 @@ __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
             busy += te - ts;
             nchunks_done += c.t_end - c.t_begin;
             const uint32_t n = c.t_end - c.t_begin;
-            const uint32_t prev = (s.C == 1) ? 0u : atomicAdd(&s.rec[c.pkg].done, n);
-            const bool pkg_finished = (prev + n == c.nchunks);
-            if (pkg_finished) {
-                s.rec[c.pkg].t1 = te;
-                s.rec[c.pkg].done = c.nchunks;
-            }
+            const bool pkg_finished = finish_chunks(s, c.pkg, n, c.nchunks, te);
             sc.last = pkg_finished ? 1u : 0u;
         }
         if (s.coverage) {  // debug: count every work-group of a finished package
@@ -228,36 +273,7 @@ __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
             __syncthreads();
         }
     }
-    // exit: per-CTA record, then the last CTA out resets the queue
-    if (threadIdx.x == 0) {
-        ecl_worker_stat w;
-        w.t_first_ns = t_first;
-        w.t_last_ns = t_last;
-        w.busy_ns = busy;
-        w.cta = blockIdx.x;
-        w.device = d;
-        w.smid = smid();
-        w.chunks = nchunks_done;
-        s.wst[blockIdx.x] = w;
-        __threadfence();
-        const unsigned int ticket = atomicAdd(&s.q->exit_count, 1u);
-        sc.last = (ticket == gridDim.x - 1) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (sc.last) {
-        __threadfence();
-        for (uint32_t i = threadIdx.x; i < s.D; i += blockDim.x) {
-            s.dev[i].word = 0ull;
-            s.dev[i].fetches = 0u;
-        }
-        if (threadIdx.x == 0) {
-            s.q->last_npkg = s.q->cursor;
-            s.q->cursor = 0ull;
-            s.q->consumed = 0ull;
-            s.q->exit_count = 0u;
-        }
-        __threadfence();
-    }
+    exit_protocol(s, d, t_first, t_last, busy, nchunks_done, &sc.last);
 }
 
 }  // namespace ecl

@@ -1,0 +1,124 @@
+"""Row-tiled tcgen05 GEMM through the C ABI vs the FP64 oracle.
+
+Plain mode: C = bf16(A) bf16(B) accumulated in FP32; the products are exact in
+FP32, so the only error is FP32 accumulation (<= K eps |A||B| elementwise,
+~sqrt(K) eps typically); the check is 1e-3 normwise (the stated tolerance)
+and 1e-4 of (|A||B|)_ij elementwise.
+Split mode: against the exact value of the three-product expansion the error
+is FP32 accumulation again; against the FP64 product of the FP32 inputs the
+normwise error is reported (the missing terms are ~2^-16 relative).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1805_02755_gb300 import build as B
+    B.build()
+    import paper_1805_02755_gb300 as E
+    return E
+
+
+def tiles(M, N):
+    return -(-M // 128) * -(-N // 256)
+
+
+def run_gemm(E, A, Bt, split=False, sched="hguided", params=(2.0, 1.0), D=0, C=0, coverage=False):
+    import torch
+    M, K = A.shape
+    N = Bt.shape[0]
+    if split:
+        a = torch.from_numpy(A).cuda()
+        b = torch.from_numpy(Bt).cuda()
+    else:  # the input cast runs in the library's own kernel
+        a = torch.empty((M, K), dtype=torch.bfloat16, device="cuda")
+        b = torch.empty((N, K), dtype=torch.bfloat16, device="cuda")
+        for src, dst in ((A, a), (Bt, b)):
+            x = torch.from_numpy(src).cuda()
+            ce = E.Engine(0)
+            pr = E.Program("cast_bf16").in_(x).out(dst).args(x, dst, x.numel())
+            ce.work_items(-(-x.numel() // 256) * 256, 256).scheduler("dynamic", (64,)).program(pr)
+            ce.run().synchronize()
+            ce.close()
+    c = torch.full((M * N + 64,), -3.0, device="cuda")
+    eng = E.Engine(0)
+    G = tiles(M, N)
+    cov = torch.zeros(G, dtype=torch.int32, device="cuda") if coverage else None
+    p = E.Program("gemm_split3" if split else "gemm_bf16").in_(a).in_(b).out(c).args(a, b, c, M, N, K)
+    eng.work_items(G * 32768, 32768).scheduler(sched, params).workers(D, C).program(p)
+    eng.set_coverage(cov)
+    eng.run().synchronize()
+    out = c.cpu().numpy()
+    assert (out[M * N:] == -3.0).all(), "wrote past C"
+    eng.close()
+    return out[: M * N].reshape(M, N), cov
+
+
+def absab(A, Bt, O):
+    a = np.abs(O.bf16_round(A).astype(np.float64))
+    b = np.abs(O.bf16_round(Bt).astype(np.float64))
+    return a @ b.T
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 128), (200, 300, 136), (1, 1, 8), (129, 257, 1000),
+                                   (512, 256, 2048)])
+def test_bf16_shapes(E, oracle_mod, M, N, K):
+    A, Bt = W.gemm_matrices(M, N, K, seed=500 + M + N + K)
+    got, _ = run_gemm(E, A, Bt)
+    ref = oracle_mod.gemm(A, Bt, 0)
+    err = np.abs(got - ref)
+    assert np.linalg.norm(err) <= 1e-3 * np.linalg.norm(ref)
+    assert (err <= 1e-4 * absab(A, Bt, oracle_mod) + 1e-30).all(), err.max()
+
+
+@pytest.mark.parametrize("sched,params,D,C", [("static", (), 1, 0), ("dynamic", (3,), 2, 0),
+                                              ("hguided", (2.0, 1.0), 4, 0), ("hguided", (1.0, 1.0), 0, 0),
+                                              ("monolithic", (), 0, 0)])
+def test_bf16_schedulers(E, oracle_mod, sched, params, D, C):
+    A, Bt = W.gemm_matrices(640, 768, 256, seed=77)
+    got, cov = run_gemm(E, A, Bt, False, sched, params, D, C, coverage=(sched != "monolithic"))
+    ref = oracle_mod.gemm(A, Bt, 0)
+    assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+    assert (np.abs(got - ref) <= 1e-4 * absab(A, Bt, oracle_mod) + 1e-30).all()
+    if cov is not None:
+        assert (cov.cpu().numpy() == 1).all()
+
+
+def test_split3_small(E, oracle_mod):
+    A, Bt = W.gemm_matrices(256, 512, 512, seed=88)
+    got, _ = run_gemm(E, A, Bt, split=True)
+    exact3 = oracle_mod.gemm(A, Bt, 2)
+    full = oracle_mod.gemm(A, Bt, 1)
+    aa = np.abs(A.astype(np.float64)) @ np.abs(Bt.astype(np.float64)).T
+    assert (np.abs(got - exact3) <= 1e-4 * aa).all()
+    e_split = np.linalg.norm(got - full) / np.linalg.norm(full)
+    plain, _ = run_gemm(E, A, Bt)
+    e_plain = np.linalg.norm(plain - full) / np.linalg.norm(full)
+    assert e_split < 2e-5 and e_split < e_plain / 50, (e_split, e_plain)
+
+
+def test_config5_full_size_sampled(E, oracle_mod):
+    M = N = K = 8192
+    A, Bt = W.gemm_matrices(M, N, K)
+    rng = np.random.default_rng(3)
+    ii = rng.integers(0, M, 512)
+    jj = rng.integers(0, N, 512)
+    got, _ = run_gemm(E, A, Bt, False, "hguided", (2.0, 1.0), 4, 0)
+    ref = oracle_mod.gemm_entries(A, Bt, 0, ii, jj)
+    aa = np.array([np.abs(oracle_mod.bf16_round(A[i]).astype(np.float64)) @
+                   np.abs(oracle_mod.bf16_round(Bt[j]).astype(np.float64)) for i, j in zip(ii, jj)])
+    e = np.abs(got[ii, jj] - ref)
+    assert (e <= 1e-4 * aa).all()
+    assert np.linalg.norm(e) <= 1e-3 * np.linalg.norm(ref)
+    del got
+    gs, _ = run_gemm(E, A, Bt, True, "hguided", (2.0, 1.0), 4, 0)
+    ref1 = oracle_mod.gemm_entries(A, Bt, 1, ii, jj)
+    rel = np.linalg.norm(gs[ii, jj] - ref1) / np.linalg.norm(ref1)
+    assert rel < 2e-5, rel
