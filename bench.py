@@ -132,8 +132,8 @@ class Mandelbrot(Workload):
         r = self.r
         t = time.perf_counter()
         O.mandelbrot(r["width"], r["height"], np.float32(r["x0"]), np.float32(r["y0"]), np.float32(r["dx"]),
-                     np.float32(r["dy"]), r["max_iter"], rows=(0, 256), threads=threads)
-        return 256 / 1024, time.perf_counter() - t, "256 of 1024 rows"
+                     np.float32(r["dy"]), r["max_iter"], threads=threads)
+        return 1.0, time.perf_counter() - t, "all 1024 rows"
 
 
 class Gaussian(Workload):
@@ -169,8 +169,8 @@ class Gaussian(Workload):
 
     def cpu_sample(self, O, threads):
         t = time.perf_counter()
-        O.gaussian(self.img, self.w, rows=(0, 256), threads=threads)
-        return 256 / self.H, time.perf_counter() - t, "256 of 8192 rows"
+        O.gaussian(self.img, self.w, rows=(0, 2048), threads=threads)
+        return 2048 / self.H, time.perf_counter() - t, "2048 of %d rows" % self.H
 
 
 class NBody(Workload):
@@ -238,13 +238,15 @@ class NBody(Workload):
         return dict(bound="alu", flops=18.0 * n * self.NFD, unit_name="samples/s", units=self.NFD)
 
     def cpu_sample(self, O, threads):
+        nb = 2048
         t = time.perf_counter()
-        O.nbody_acc(self.pos, self.EPS2, bodies=(0, 128), threads=threads)
-        O.nbody_energy_grad(self.pos, self.EPS2, bodies=(0, 128), threads=threads)
-        O.nbody_potential(self.pos, self.EPS2, bodies=(0, 128), threads=threads)
+        O.nbody_acc(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
+        O.nbody_energy_grad(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
+        O.nbody_potential(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
         secs = time.perf_counter() - t
-        # acc + grad rows are each 1/n of their program; the potential stands in for the energy rows
-        return 128 / self.n, secs, "128 of 65536 bodies of the force, adjoint and potential rows"
+        # force and adjoint rows are each nb/n of their program; full potential rows stand in
+        # for the energy rows (twice the i<j work, so the sample overstates the energy's cost)
+        return nb / self.n, secs, "%d of %d bodies of the force, adjoint and potential rows" % (nb, self.n)
 
 
 class Binomial(Workload):
@@ -298,7 +300,7 @@ class Binomial(Workload):
 
     def cpu_sample(self, O, threads):
         t = time.perf_counter()
-        k = 4 * threads
+        k = 512 * threads
         o = self.o
         O.binomial(o["S"][:k], o["K"][:k], o["T"][:k], o["sigma"][:k], o["steps"][:k], o["r"], threads=threads)
         return k / self.n, time.perf_counter() - t, "%d of %d options (price, delta, vega)" % (k, self.n)
@@ -365,12 +367,14 @@ class Gemm(Workload):
 
     def cpu_sample(self, O, threads):
         rng = W.rng(5)
-        ii = rng.integers(0, self.M, 64)
-        jj = rng.integers(0, self.N, 64)
+        ne = 4096
+        ii = rng.integers(0, self.M, ne)
+        jj = rng.integers(0, self.N, ne)
         t = time.perf_counter()
         O.gemm_entries(self.A, self.Bt, 0, ii, jj, threads=threads)
         O.gemm_entries(self.A, self.Bt, 2, ii, jj, threads=threads)
-        return 64 / (self.M * self.N), time.perf_counter() - t, "64 of %d entries, both modes" % (self.M * self.N)
+        return ne / (self.M * self.N), time.perf_counter() - t, "%d of %d entries, both modes" % (
+            ne, self.M * self.N)
 
 
 class MultiEngine:

@@ -117,8 +117,15 @@ def test_config5_full_size_sampled(E, oracle_mod):
     e = np.abs(got[ii, jj] - ref)
     assert (e <= 1e-4 * aa).all()
     assert np.linalg.norm(e) <= 1e-3 * np.linalg.norm(ref)
+    ref1 = oracle_mod.gemm_entries(A, Bt, 1, ii, jj)
+    rel_plain = np.linalg.norm(got[ii, jj] - ref1) / np.linalg.norm(ref1)
     del got
     gs, _ = run_gemm(E, A, Bt, True, "hguided", (2.0, 1.0), 4, 0)
-    ref1 = oracle_mod.gemm_entries(A, Bt, 1, ii, jj)
+    ref3 = oracle_mod.gemm_entries(A, Bt, 2, ii, jj)
+    aa3 = np.array([np.abs(A[i].astype(np.float64)) @ np.abs(Bt[j].astype(np.float64)) for i, j in zip(ii, jj)])
+    assert (np.abs(gs[ii, jj] - ref3) <= 1e-4 * aa3).all()
     rel = np.linalg.norm(gs[ii, jj] - ref1) / np.linalg.norm(ref1)
-    assert rel < 2e-5, rel
+    # three products win back most of FP32 accuracy; the tensor-core FP32
+    # accumulation over 3 x 8192 products then dominates what is left
+    print("normwise error vs FP64 of FP32 inputs: plain %.3e, split3 %.3e" % (rel_plain, rel))
+    assert rel < rel_plain / 20 and rel < 1e-4, (rel, rel_plain)

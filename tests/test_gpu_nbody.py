@@ -62,7 +62,9 @@ def run_acc(E, pos, lws=64, sched="hguided", params=(2.0, 1.0), D=0, C=0, covera
 def check_acc(got, ref, pos, idx):
     err = np.abs(got[idx, :3] - ref[idx]).max(1)
     c = cond(pos, idx)
-    assert (err / c).max() <= RTOL, (err / c).max()
+    assert (err[c == 0] == 0).all()  # a lone body feels no force
+    k = c > 0
+    assert (err[k] / c[k]).max(initial=0.0) <= RTOL, (err[k] / c[k]).max()
     assert np.linalg.norm(got[idx, :3] - ref[idx]) <= RTOL * np.linalg.norm(ref[idx])
 
 
