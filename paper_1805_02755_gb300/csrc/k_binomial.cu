@@ -4,11 +4,11 @@
 //
 // One warp (the work-group, lws 32) prices one option.  Level t of the
 // lattice holds nodes j = 0..t; node j lives in lane j / R, register slot
-// j % R, with R in {64, 32, ..., 1}.  A backward step needs node j+1: in the
-// same lane except for the last slot, which one shuffle per level brings
-// from the next lane.  When the live nodes fit in half the registers the
-// warp repacks to R/2 (one shuffle per slot), so at least half of every
-// lane's slots stay live.
+// j % R, where the width R steps down 64, 56, 48, ..., 2, 1 as the lattice
+// shrinks.  A backward step needs node j+1: in the same lane except for the
+// last slot, which one shuffle per level brings from the next lane.  When
+// the live nodes fit in the next width the warp repacks its registers
+// through a padded shared buffer, so ~90% of the computed slots stay live.
 //
 // Arithmetic (exact in real numbers, arranged for FP32):
 //   p = 1/2 + q,  q = (expm1(r dt) - 2 sinh^2(a/2)) / (2 sinh a),  a = sigma sqrt(dt)
@@ -57,6 +57,21 @@ struct Lat {
     int shift;     // power of two still to remove from the result
 };
 
+// Lane widths (nodes per lane) the warp steps through as the lattice shrinks.
+// Going from width R to the next width R' happens when the live nodes fit in
+// 32 R'; steps of about 1/8 keep ~90% of the computed slots live.
+__host__ __device__ constexpr int width_at(int i)
+{
+    return i == 0 ? 64 : i == 1 ? 56 : i == 2 ? 48 : i == 3 ? 40 : i == 4 ? 32 : i == 5 ? 28 : i == 6 ? 24
+         : i == 7 ? 20 : i == 8 ? 16 : i == 9 ? 14 : i == 10 ? 12 : i == 11 ? 10 : i == 12 ? 8 : i == 13 ? 7
+         : i == 14 ? 6 : i == 15 ? 5 : i == 16 ? 4 : i == 17 ? 3 : i == 18 ? 2 : i == 19 ? 1 : 0;
+}
+constexpr int kMaxR = 64;
+constexpr int kMaxSteps = kWarp * kMaxR;               // deepest lattice: 2048 steps
+constexpr int kShNodes = kMaxSteps + 1 + kMaxSteps / 32 + 32;  // leaves 0..N with padding
+
+__device__ __forceinline__ int shidx(int j) { return j + (j >> 5); }  // avoids bank conflicts
+
 template <int R, bool G>
 __device__ __forceinline__ void level(float (&B)[R], float (&D)[R], float (&V)[R], Lat &L)
 {
@@ -93,68 +108,75 @@ __device__ __forceinline__ void level(float (&B)[R], float (&D)[R], float (&V)[R
     }
 }
 
-// Runs levels with R slots per lane until the live nodes fit in R/2, then
-// repacks and continues with R/2.
-template <int R, bool G>
-__device__ __forceinline__ void phase(float (&B)[R], float (&D)[R], float (&V)[R], Lat &L)
+// One tree from width R to width R2 through the warp's shared buffer.
+template <int R, int R2>
+__device__ __forceinline__ void repack(const float (&x)[R], float (&y)[R2], float *sh, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int limit = (R > 1) ? kWarp * (R / 2) : 1;
-    while (L.active > limit) level<R, G>(B, D, V, L);
-    if constexpr (R > 1) {
-        constexpr int H = R / 2;
-        float b2[H], d2[H], v2[H];
-        const int src = lane >> 1;
-        const bool odd = lane & 1;
+    __syncwarp();
 #pragma unroll
-        for (int s = 0; s < H; ++s) {
-            const float lo = __shfl_sync(kFull, B[s], src), hi = __shfl_sync(kFull, B[H + s], src);
-            b2[s] = odd ? hi : lo;
-            if (G) {
-                const float dl = __shfl_sync(kFull, D[s], src), dh = __shfl_sync(kFull, D[H + s], src);
-                const float vl = __shfl_sync(kFull, V[s], src), vh = __shfl_sync(kFull, V[H + s], src);
-                d2[s] = odd ? dh : dl;
-                v2[s] = odd ? vh : vl;
-            }
+    for (int s = 0; s < R; ++s) sh[shidx(lane * R + s)] = x[s];
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < R2; ++s) y[s] = sh[shidx(lane * R2 + s)];
+}
+
+// Levels at width width_at(WI) until the live nodes fit the next width, then
+// repack and continue; lane 0 slot 0 ends up holding the root.
+template <int WI, bool G>
+__device__ __forceinline__ void phase(float (&B)[width_at(WI)], float (&D)[width_at(WI)], float (&V)[width_at(WI)],
+                                      Lat &L, float *sh, int lane)
+{
+    constexpr int R = width_at(WI);
+    constexpr int R2 = width_at(WI + 1);
+    const int limit = R2 ? kWarp * R2 : 1;
+    while (L.active > limit) level<R, G>(B, D, V, L);
+    if constexpr (R2 > 0) {
+        float b2[R2], d2[R2], v2[R2];
+        repack<R, R2>(B, b2, sh, lane);
+        if (G) {
+            repack<R, R2>(D, d2, sh, lane);
+            repack<R, R2>(V, v2, sh, lane);
         }
-        phase<H, G>(b2, d2, v2, L);
-        if (lane == 0) {
-            B[0] = b2[0];
-            if (G) {
-                D[0] = d2[0];
-                V[0] = v2[0];
-            }
+        phase<WI + 1, G>(b2, d2, v2, L, sh, lane);
+        B[0] = b2[0];
+        if (G) {
+            D[0] = d2[0];
+            V[0] = v2[0];
         }
     }
 }
 
-// Leaves and the first backward level for R slots per lane, then the rest.
-template <int R, bool G>
-__device__ __forceinline__ void price_option(const BinoParams &p, int64_t o)
+template <bool G>
+__device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, float *sh)
 {
     const int lane = threadIdx.x & 31;
     const float S = __ldg(p.S + o), K = __ldg(p.K + o), T = __ldg(p.T + o), sig = __ldg(p.sigma + o);
     const int N = __ldg(p.steps + o);
+    if (N < 1 || N > kMaxSteps) {  // outside the supported depths: NaN results
+        if (lane == 0) {
+            p.price[o] = __int_as_float(0x7fc00000);
+            if (G) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+        }
+        return;
+    }
     const float dt = T / (float)N;
     const float sdt = sqrtf(dt);
     const float a = sig * sdt;
-    const float sh = sinhf(0.5f * a);
-    const float num = expm1f(p.r * dt) - 2.0f * sh * sh;
+    const float sh2 = sinhf(0.5f * a);
+    const float num = expm1f(p.r * dt) - 2.0f * sh2 * sh2;
     const float s1 = sinhf(a);
     const float q = num / (2.0f * s1);
     Lat L;
     L.q2 = 2.0f * q;
     L.q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));
-    L.active = N;  // nodes of level N-1
-    L.rescale = 0;
+    L.active = N;   // nodes of level N-1
+    L.rescale = 1;  // that level is formed from the leaves below
     L.shift = N;
     const bool put = S > K;  // price the out-of-the-money side, then parity
-    float B[R], D[R], V[R];
-    // level N-1 directly from the leaves j and j+1
-    float lb = 0.f, ld = 0.f, lv = 0.f;  // leaf j of the previous slot (j+1 of this one)
-#pragma unroll
-    for (int s = R; s >= 0; --s) {
-        const int j = lane * R + s;
+    // leaves 0..N (zero beyond N) into the shared buffers, lane-strided
+    float *shb = sh, *shd = sh + kShNodes, *shv = sh + 2 * kShNodes;
+    __syncwarp();
+    for (int j = lane; j <= kMaxSteps; j += kWarp) {
         float b = 0.f, d = 0.f, v = 0.f;
         if (j <= N) {
             const float m = (float)(2 * j - N);
@@ -168,20 +190,29 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o)
                 }
             }
         }
-        if (s < R) {
-            const float diff = lb - b;
-            B[s] = fmaf(L.q2, diff, lb + b);
-            if (G) {
-                D[s] = fmaf(L.q2, ld - d, ld + d);
-                V[s] = fmaf(L.q2p, diff, fmaf(L.q2, lv - v, lv + v));
-            }
+        shb[shidx(j)] = b;
+        if (G) {
+            shd[shidx(j)] = d;
+            shv[shidx(j)] = v;
         }
-        lb = b;
-        ld = d;
-        lv = v;
     }
-    L.rescale = 1;
-    phase<R, G>(B, D, V, L);
+    __syncwarp();
+    // level N-1 at width 64: node j from leaves j and j+1
+    float B[kMaxR], D[kMaxR], V[kMaxR];
+#pragma unroll
+    for (int s = 0; s < kMaxR; ++s) {
+        const int j = lane * kMaxR + s;
+        const float lb = shb[shidx(j + 1)], b = shb[shidx(j)];
+        const float diff = lb - b;
+        B[s] = fmaf(L.q2, diff, lb + b);
+        if (G) {
+            const float ld = shd[shidx(j + 1)], d = shd[shidx(j)];
+            const float lv = shv[shidx(j + 1)], v = shv[shidx(j)];
+            D[s] = fmaf(L.q2, ld - d, ld + d);
+            V[s] = fmaf(L.q2p, diff, fmaf(L.q2, lv - v, lv + v));
+        }
+    }
+    phase<0, G>(B, D, V, L, sh, lane);
     if (lane == 0) {
         // remove the remaining 2^shift (exact), then discount
         const float disc = expf(-p.r * T);
@@ -197,44 +228,27 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o)
 }
 
 template <bool G>
-__device__ void dispatch(const BinoParams &p, int64_t o)
-{
-    const int N = __ldg(p.steps + o);
-    if (N < 1 || N > 2048) {  // outside the supported depths: NaN results
-        if ((threadIdx.x & 31) == 0) {
-            p.price[o] = __int_as_float(0x7fc00000);
-            if (G) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
-        }
-        return;
-    }
-    if (N > 1024) price_option<64, G>(p, o);
-    else if (N > 512) price_option<32, G>(p, o);
-    else if (N > 256) price_option<16, G>(p, o);
-    else if (N > 128) price_option<8, G>(p, o);
-    else if (N > 64) price_option<4, G>(p, o);
-    else if (N > 32) price_option<2, G>(p, o);
-    else price_option<1, G>(p, o);
-}
-
-template <bool G>
 struct BinoBody {
     using Params = BinoParams;
     Params p;
+    float *sh;
 
     static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len) { return (uint32_t)len; }
 
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
         const int64_t o = (int64_t)(off + t);
-        if (o < p.n) dispatch<G>(p, o);
+        if (o < p.n) price_option<G>(p, o, sh);
     }
 };
 
 template <bool G>
 __global__ void __launch_bounds__(kWarp) k_binomial(BinoParams prm, SchedArgs s)
 {
+    __shared__ float sh[(G ? 3 : 1) * kShNodes];
     BinoBody<G> b;
     b.p = prm;
+    b.sh = sh;
     drive(s, b);
 }
 

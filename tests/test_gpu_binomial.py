@@ -71,9 +71,10 @@ def test_depth_ranges(E, oracle_mod, lo, hi):
 
 
 def test_every_depth_boundary(E, oracle_mod):
-    # depths at every register-blocking switch (32, 64, ..., 1024) and the extremes
-    steps = np.array([1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1023,
-                      1024, 1025, 2047, 2048], dtype=np.int32)
+    # depths at every lane-width switch (32 x {1, 2, ..., 56, 64}) and the extremes
+    widths = [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64]
+    steps = sorted({v for w in widths for v in (32 * w - 1, 32 * w, 32 * w + 1) if 1 <= v <= 2048} | {1, 2, 3})
+    steps = np.array(steps, dtype=np.int32)
     o = W.binomial_options(len(steps), seed=41)
     o["steps"] = steps
     price, gr, _ = run_bino(E, o)
