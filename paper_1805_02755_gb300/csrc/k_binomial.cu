@@ -59,12 +59,18 @@ struct Lat {
 
 // Lane widths (nodes per lane) the warp steps through as the lattice shrinks.
 // Going from width R to the next width R' happens when the live nodes fit in
-// 32 R'; steps of about 1/8 keep ~90% of the computed slots live.
+// 32 R'.  Price only: steps of about 1/8 (~91% of the computed slots live for
+// depths U{256..2048}).  With greeks every slot costs 10 instructions instead
+// of 3, so the unrolled level code of many widths would overflow the
+// instruction cache; a shorter list keeps ~82% live at 2/5 of the code.
+template <bool G>
 __host__ __device__ constexpr int width_at(int i)
 {
-    return i == 0 ? 64 : i == 1 ? 56 : i == 2 ? 48 : i == 3 ? 40 : i == 4 ? 32 : i == 5 ? 28 : i == 6 ? 24
-         : i == 7 ? 20 : i == 8 ? 16 : i == 9 ? 14 : i == 10 ? 12 : i == 11 ? 10 : i == 12 ? 8 : i == 13 ? 7
-         : i == 14 ? 6 : i == 15 ? 5 : i == 16 ? 4 : i == 17 ? 3 : i == 18 ? 2 : i == 19 ? 1 : 0;
+    return G ? (i == 0 ? 64 : i == 1 ? 48 : i == 2 ? 32 : i == 3 ? 24 : i == 4 ? 16 : i == 5 ? 8 : i == 6 ? 4
+              : i == 7 ? 2 : i == 8 ? 1 : 0)
+             : (i == 0 ? 64 : i == 1 ? 56 : i == 2 ? 48 : i == 3 ? 40 : i == 4 ? 32 : i == 5 ? 28 : i == 6 ? 24
+              : i == 7 ? 20 : i == 8 ? 16 : i == 9 ? 14 : i == 10 ? 12 : i == 11 ? 10 : i == 12 ? 8 : i == 13 ? 7
+              : i == 14 ? 6 : i == 15 ? 5 : i == 16 ? 4 : i == 17 ? 3 : i == 18 ? 2 : i == 19 ? 1 : 0);
 }
 constexpr int kMaxR = 64;
 constexpr int kMaxSteps = kWarp * kMaxR;               // deepest lattice: 2048 steps
@@ -123,11 +129,11 @@ __device__ __forceinline__ void repack(const float (&x)[R], float (&y)[R2], floa
 // Levels at width width_at(WI) until the live nodes fit the next width, then
 // repack and continue; lane 0 slot 0 ends up holding the root.
 template <int WI, bool G>
-__device__ __forceinline__ void phase(float (&B)[width_at(WI)], float (&D)[width_at(WI)], float (&V)[width_at(WI)],
-                                      Lat &L, float *sh, int lane)
+__device__ __forceinline__ void phase(float (&B)[width_at<G>(WI)], float (&D)[width_at<G>(WI)],
+                                      float (&V)[width_at<G>(WI)], Lat &L, float *sh, int lane)
 {
-    constexpr int R = width_at(WI);
-    constexpr int R2 = width_at(WI + 1);
+    constexpr int R = width_at<G>(WI);
+    constexpr int R2 = width_at<G>(WI + 1);
     const int limit = R2 ? kWarp * R2 : 1;
     while (L.active > limit) level<R, G>(B, D, V, L);
     if constexpr (R2 > 0) {

@@ -63,12 +63,20 @@ __device__ __forceinline__ ChunkGeom geom(const GaussParams &p, uint64_t off, ui
     g.p0 = (int64_t)(off * p.lws);
     g.p1 = (int64_t)((off + len) * p.lws);
     if (g.p1 > npx) g.p1 = npx;
-    const int64_t r0 = g.p0 / p.W, r1 = (g.p1 - 1) / p.W;
-    const int64_t nt = (p.W + kTW - 1) / kTW;
-    const int64_t b = t / nt, c = t % nt;
-    g.y0 = r0 + b * kRB;
+    const uint32_t nt = (uint32_t)((p.W + kTW - 1) / kTW);
+    int64_t r0, r1;
+    if (npx < (int64_t)0x7fffffff) {  // 32-bit divisions: a few instructions instead of ~100
+        const uint32_t W = (uint32_t)p.W;
+        r0 = (uint32_t)g.p0 / W;
+        r1 = (uint32_t)(g.p1 - 1) / W;
+    } else {
+        r0 = g.p0 / p.W;
+        r1 = (g.p1 - 1) / p.W;
+    }
+    const uint32_t b = t / nt, c = t % nt;
+    g.y0 = r0 + (int64_t)b * kRB;
     g.rows = min((int64_t)kRB, r1 + 1 - g.y0);
-    g.x0 = c * kTW;
+    g.x0 = (int64_t)c * kTW;
     return g;
 }
 
@@ -165,15 +173,23 @@ struct Gauss31Body {
         const int c4 = threadIdx.x % kSC;  // fixed 16-byte column chunk per thread
         const int64_t xs = g.x0 - 16 + 4 * c4;
         const bool vec = vec_ok && xs >= 0 && xs + 4 <= p.W;
-        for (int k = threadIdx.x / kSC; k < kNIN; k += kBlock / kSC) {
-            const int64_t ys = clampl(g.y0 - 15 + k, 0, p.H - 1);
-            const float *row = p.in + ys * p.W;
-            float *dst = &st[k][4 * c4];
-            if (vec) {
-                cp_async16(dst, row + xs);
-            } else {
+        const int k0 = threadIdx.x / kSC;
+        const int64_t ylo = g.y0 - 15 + k0;
+        if (vec && ylo >= 0 && g.y0 - 15 + kNIN <= p.H) {  // interior rows: pointer steps, no clamps
+            const float *src = p.in + ylo * p.W + xs;
+            const int64_t step = (int64_t)(kBlock / kSC) * p.W;
+            for (int k = k0; k < kNIN; k += kBlock / kSC, src += step) cp_async16(&st[k][4 * c4], src);
+        } else {
+            for (int k = k0; k < kNIN; k += kBlock / kSC) {
+                const int64_t ys = clampl(g.y0 - 15 + k, 0, p.H - 1);
+                const float *row = p.in + ys * p.W;
+                float *dst = &st[k][4 * c4];
+                if (vec) {
+                    cp_async16(dst, row + xs);
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dst[j] = __ldg(row + clampl(xs + j, 0, p.W - 1));
+                    for (int j = 0; j < 4; ++j) dst[j] = __ldg(row + clampl(xs + j, 0, p.W - 1));
+                }
             }
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");

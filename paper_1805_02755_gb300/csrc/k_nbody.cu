@@ -9,9 +9,11 @@
 //   nbody_fd       central differences of E in sampled coordinates
 //
 // One chunk = one work-group of lws bodies (lws 32..256, a power of two).
-// The CTA has 256 threads: thread t owns body t % lws of the work-group and
-// the j-slice t / lws; j-bodies are staged in shared memory 256 at a time
-// (tiles on an absolute 256-body grid).  Each thread sums the pair terms of
+// The CTA has 256 threads.  Force kernels: thread t owns two bodies of the
+// work-group (t % (lws/2) and that + lws/2, computed together in packed
+// FP32x2 arithmetic) and the j-slice t / (lws/2).  Energy: thread t owns
+// body t % lws and the j-slice t / lws.  j-bodies are staged in shared
+// memory 256 at a time (tiles on an absolute 256-body grid).  Each thread sums the pair terms of
 // one tile in FP32, then adds the tile sum to its running FP32 total
 // (two-level summation); the slices of a body are added in slice order.
 // The energy and finite-difference sums are FP32 pair terms accumulated in
@@ -50,12 +52,61 @@ __device__ __forceinline__ void stage_tile(float4 *sh, const float4 *pos, int64_
     sh[threadIdx.x] = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Packed FP32x2 arithmetic (sm_100+): one instruction, two lanes of work.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Stage j-tile `tile` duplicated for packed use: (x,x,y,y) and (z,z,m,m).
+__device__ __forceinline__ void stage_tile2(float4 *shxy, float4 *shzm, const float4 *pos, int64_t n, int64_t tile)
+{
+    const int64_t j = tile * kTile + threadIdx.x;
+    const float4 q = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    shxy[threadIdx.x] = make_float4(q.x, q.x, q.y, q.y);
+    shzm[threadIdx.x] = make_float4(q.z, q.z, q.w, q.w);
+}
+
+// Force loop: thread t owns bodies (b, b + lws/2) of the work-group, b =
+// t % (lws/2), and the j-slice t / (lws/2); both bodies advance together in
+// packed FP32x2 arithmetic, each exactly as the scalar sequence
+//   d = r_j - r_i, r2 = dx dx + (dy dy + (dz dz + eps2)), inv = rsqrt(r2),
+//   s = (m_j inv)(inv inv), a += s d.
 template <uint32_t MODE>
 struct ForceBody {
     using Params = NBodyParams;
     Params p;
-    float4 *sh;   // [kTile] j-bodies
-    float4 *red;  // [kBlock] slice partials
+    float4 *shxy, *shzm;  // [kTile] duplicated j-bodies
+    float4 *red;          // [2 * kBlock] slice partials
 
     static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
     {
@@ -64,78 +115,97 @@ struct ForceBody {
 
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
-        const uint32_t lws = p.lws;
-        const uint32_t S = kBlock / lws;             // j-slices
-        const uint32_t b = threadIdx.x % lws, s = threadIdx.x / lws;
-        const int64_t i = (int64_t)(off + t) * lws + b;
-        const bool valid = i < p.n;
-        const float4 pi = valid ? __ldg(p.pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const uint32_t span = kTile / S;             // j's of one tile in this slice
-        float ax = 0.f, ay = 0.f, az = 0.f, pot = 0.f;
+        const uint32_t half = p.lws / 2;
+        const uint32_t S = kBlock / half;            // j-slices
+        const uint32_t b = threadIdx.x % half, s = threadIdx.x / half;
+        const int64_t i0 = (int64_t)(off + t) * p.lws + b, i1 = i0 + half;
+        const bool v0 = i0 < p.n, v1 = i1 < p.n;
+        const float4 p0 = v0 ? __ldg(p.pos + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 p1 = v1 ? __ldg(p.pos + i1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const f2 X = pk(p0.x, p1.x), Y = pk(p0.y, p1.y), Z = pk(p0.z, p1.z);
+        const f2 EPS = pk(p.eps2, p.eps2);
+        const uint32_t span = kTile / S;
+        f2 AX = 0, AY = 0, AZ = 0, POT = 0;
         const int64_t ntiles = (p.n + kTile - 1) / kTile;
         for (int64_t tile = 0; tile < ntiles; ++tile) {
             __syncthreads();
-            stage_tile(sh, p.pos, p.n, tile);
+            stage_tile2(shxy, shzm, p.pos, p.n, tile);
             __syncthreads();
-            float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
-            const float4 *q = sh + s * span;
+            f2 TX = 0, TY = 0, TZ = 0, TP = 0;
+            const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + s * span);
+            const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + s * span);
 #pragma unroll 8
             for (uint32_t k = 0; k < span; ++k) {
-                const float4 pj = q[k];
-                const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2)));
-                const float inv = rsqrtf(r2);
-                const float mi = pj.w * inv;
-                if (MODE == NB_ADJ) tp += mi;
-                const float sc = mi * (inv * inv);
-                tx = fmaf(sc, dx, tx);
-                ty = fmaf(sc, dy, ty);
-                tz = fmaf(sc, dz, tz);
+                const ulonglong2 xy = qxy[k], zm = qzm[k];
+                const f2 dx = sub2(xy.x, X), dy = sub2(xy.y, Y), dz = sub2(zm.x, Z);
+                const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, EPS)));
+                float r0, r1;
+                upk(r2, r0, r1);
+                const f2 inv = pk(rsqrtf(r0), rsqrtf(r1));
+                const f2 mi = mul2(zm.y, inv);
+                if (MODE == NB_ADJ) TP = add2(TP, mi);
+                const f2 sc = mul2(mi, mul2(inv, inv));
+                TX = fma2(sc, dx, TX);
+                TY = fma2(sc, dy, TY);
+                TZ = fma2(sc, dz, TZ);
             }
-            ax += tx;
-            ay += ty;
-            az += tz;
-            if (MODE == NB_ADJ) pot += tp;
+            AX = add2(AX, TX);
+            AY = add2(AY, TY);
+            AZ = add2(AZ, TZ);
+            if (MODE == NB_ADJ) POT = add2(POT, TP);
         }
         // combine the slices of each body in slice order
+        float ax0, ax1, ay0, ay1, az0, az1, pt0, pt1;
+        upk(AX, ax0, ax1);
+        upk(AY, ay0, ay1);
+        upk(AZ, az0, az1);
+        upk(POT, pt0, pt1);
         __syncthreads();
-        red[threadIdx.x] = make_float4(ax, ay, az, pot);
+        red[threadIdx.x] = make_float4(ax0, ay0, az0, pt0);
+        red[kBlock + threadIdx.x] = make_float4(ax1, ay1, az1, pt1);
         __syncthreads();
-        if (s == 0 && valid) {
-            float4 a = red[b];
-            for (uint32_t q = 1; q < S; ++q) {
-                const float4 r = red[q * lws + b];
-                a.x += r.x;
-                a.y += r.y;
-                a.z += r.z;
-                a.w += r.w;
-            }
-            if (MODE == NB_ACC) {
-                p.out_acc[i] = make_float4(a.x, a.y, a.z, 0.f);
-            } else if (MODE == NB_STEP) {
-                const float4 v = __ldg(p.vel + i);
-                const float h = 0.5f * p.dt * p.dt;
-                p.out_pos[i] = make_float4(pi.x + v.x * p.dt + a.x * h, pi.y + v.y * p.dt + a.y * h,
-                                           pi.z + v.z * p.dt + a.z * h, pi.w);
-                p.out_vel[i] = make_float4(v.x + a.x * p.dt, v.y + a.y * p.dt, v.z + a.z * p.dt, v.w);
-            } else {
-                // the self term j == i added m_i / sqrt(eps2) to the potential sum
-                const float self = pi.w * rsqrtf(p.eps2);
-                const float g = __ldg(p.grad_E);
-                p.out_grad[i] = make_float4(-g * pi.w * a.x, -g * pi.w * a.y, -g * pi.w * a.z, -g * (a.w - self));
+        if (s < 2) {  // slice-0 thread finishes body b, slice-1 thread body b + half
+            const int64_t i = s == 0 ? i0 : i1;
+            if (i < p.n) {
+                const float4 pi = s == 0 ? p0 : p1;
+                const float4 *r = red + (s == 0 ? 0 : kBlock);
+                float4 a = r[b];
+                for (uint32_t q = 1; q < S; ++q) {
+                    const float4 e = r[q * half + b];
+                    a.x += e.x;
+                    a.y += e.y;
+                    a.z += e.z;
+                    a.w += e.w;
+                }
+                if (MODE == NB_ACC) {
+                    p.out_acc[i] = make_float4(a.x, a.y, a.z, 0.f);
+                } else if (MODE == NB_STEP) {
+                    const float4 v = __ldg(p.vel + i);
+                    const float h = 0.5f * p.dt * p.dt;
+                    p.out_pos[i] = make_float4(pi.x + v.x * p.dt + a.x * h, pi.y + v.y * p.dt + a.y * h,
+                                               pi.z + v.z * p.dt + a.z * h, pi.w);
+                    p.out_vel[i] = make_float4(v.x + a.x * p.dt, v.y + a.y * p.dt, v.z + a.z * p.dt, v.w);
+                } else {
+                    // the self term j == i added m_i / sqrt(eps2) to the potential sum
+                    const float self = pi.w * rsqrtf(p.eps2);
+                    const float g = __ldg(p.grad_E);
+                    p.out_grad[i] = make_float4(-g * pi.w * a.x, -g * pi.w * a.y, -g * pi.w * a.z, -g * (a.w - self));
+                }
             }
         }
     }
 };
 
 // ---------------------------------------------------------------- energy
+constexpr uint32_t kESeg = 8;  // chunks (j-segments) per work-group of the energy
+
 struct EnergyParams {
     const float4 *pos;
     int64_t n;
     float eps2;
     double *out_E;
-    double *partial;     // one per work-group
-    unsigned *counter;   // work-groups finished in this run (reset by the last)
+    double *partial;     // one per (work-group, segment)
+    unsigned *counter;   // chunks finished in this run (reset by the last)
     uint64_t G;
     uint32_t lws;
 };
@@ -153,9 +223,12 @@ struct EnergyBody {
     float4 *sh;
     double *dsh;  // [kBlock / 32] warp sums, then [1] flag
 
+    // Rows i < j make early work-groups far costlier than late ones; each
+    // work-group's j-range is cut into kESeg tile-aligned segments so that no
+    // single chunk dominates the run.
     static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
     {
-        return one_chunk_per_wg(len);
+        return (uint32_t)(len * kESeg);
     }
 
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
@@ -163,7 +236,8 @@ struct EnergyBody {
         const uint32_t lws = p.lws;
         const uint32_t S = kBlock / lws;
         const uint32_t b = threadIdx.x % lws, s = threadIdx.x / lws;
-        const uint64_t wg = off + t;
+        const uint64_t wg = off + t / kESeg;
+        const uint32_t seg = t % kESeg;
         const int64_t i0 = (int64_t)wg * lws;
         const int64_t i = i0 + b;
         const bool valid = i < p.n;
@@ -171,8 +245,10 @@ struct EnergyBody {
         const uint32_t span = kTile / S;
         double e = 0.0;
         const int64_t ntiles = (p.n + kTile - 1) / kTile;
-        // rows i < j only: tiles from the one holding this work-group onwards
-        for (int64_t tile = i0 / kTile; tile < ntiles; ++tile) {
+        // rows i < j only: tiles from the one holding this work-group onwards, this segment's share
+        const int64_t tfirst = i0 / kTile, nt = ntiles - tfirst;
+        const int64_t ta = tfirst + nt * seg / kESeg, tb = tfirst + nt * (seg + 1) / kESeg;
+        for (int64_t tile = ta; tile < tb; ++tile) {
             __syncthreads();
             stage_tile(sh, p.pos, p.n, tile);
             __syncthreads();
@@ -209,18 +285,19 @@ struct EnergyBody {
         if (threadIdx.x == 0) {
             double w = 0.0;
             for (int q = 0; q < kBlock / 32; ++q) w += dsh[q];
-            p.partial[wg] = w;
+            p.partial[wg * kESeg + seg] = w;
             __threadfence();
             const unsigned before = atomicAdd(p.counter, 1u);
-            dsh[0] = (before + 1 == (unsigned)p.G) ? 1.0 : 0.0;
+            dsh[0] = (before + 1 == (unsigned)(p.G * kESeg)) ? 1.0 : 0.0;
         }
         __syncthreads();
-        if (dsh[0] != 0.0) {  // last work-group of the run: sum the partials in order
+        if (dsh[0] != 0.0) {  // last chunk of the run: sum the partials in order
             __threadfence();
             double acc = 0.0;
-            const uint64_t per = (p.G + kBlock - 1) / kBlock;
+            const uint64_t np = p.G * kESeg;
+            const uint64_t per = (np + kBlock - 1) / kBlock;
             const uint64_t a = threadIdx.x * per;
-            const uint64_t z = min(p.G, a + per);
+            const uint64_t z = min(np, a + per);
             for (uint64_t w = a; w < z; ++w) acc += *((volatile double *)p.partial + w);
             __syncthreads();
             __shared__ double tree[kBlock];
@@ -313,11 +390,13 @@ struct FDBody {
 template <uint32_t MODE>
 __global__ void __launch_bounds__(kBlock) k_nbody_force(NBodyParams prm, SchedArgs s)
 {
-    __shared__ float4 sh[kTile];
-    __shared__ float4 red[kBlock];
+    __shared__ __align__(16) float4 shxy[kTile];
+    __shared__ __align__(16) float4 shzm[kTile];
+    __shared__ float4 red[2 * kBlock];
     ForceBody<MODE> b;
     b.p = prm;
-    b.sh = sh;
+    b.shxy = shxy;
+    b.shzm = shzm;
     b.red = red;
     drive(s, b);
 }
@@ -391,6 +470,8 @@ bool out4_ok(const KArgs &a, int i, int64_t n) { return a.bytes[i] >= (uint64_t)
 uint64_t grain1(const KArgs &, uint64_t, uint32_t) { return 1; }
 
 uint32_t nchunks_wg(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+uint32_t nchunks_energy(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)(len * kESeg); }
 
 // ---- nbody (Listing 2 order): in_pos, in_vel, bodies, del_t, esp_sqr, out_pos, out_vel
 ecl_status v_step(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
@@ -488,7 +569,7 @@ ecl_status v_energy(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err
         err = "out_energy must be an aligned double[1]";
         return ECL_ERR_BUFFER;
     }
-    if (gws / lws > 0xffffffffull) {
+    if (gws / lws > 0xffffffffull / kESeg) {
         err = "too many work-groups";
         return ECL_ERR_SIZE;
     }
@@ -498,7 +579,7 @@ ecl_status v_energy(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err
 ecl_status l_energy(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
     const uint64_t G = c.gws / c.lws;
-    char *ws = (char *)workspace_get(c.ws, 256 + G * sizeof(double), err);
+    char *ws = (char *)workspace_get(c.ws, 256 + G * kESeg * sizeof(double), err);
     if (!ws) return ECL_ERR_CUDA;
     EnergyParams p{};
     p.pos = a.buf<const float4>(0);
@@ -580,7 +661,7 @@ extern const KernelDesc kNBodyAdjoint = {
 extern const KernelDesc kNBodyEnergy = {
     "nbody_energy", 4,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_energy", A_BUF_OUT}},
-    1, 0, kBlock, 0, v_energy, grain1, nchunks_wg, o_energy, l_energy,
+    1, 0, kBlock, 0, v_energy, grain1, nchunks_energy, o_energy, l_energy,
 };
 
 extern const KernelDesc kNBodyFD = {

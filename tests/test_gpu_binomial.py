@@ -72,7 +72,7 @@ def test_depth_ranges(E, oracle_mod, lo, hi):
 
 def test_every_depth_boundary(E, oracle_mod):
     # depths at every lane-width switch (32 x {1, 2, ..., 56, 64}) and the extremes
-    widths = [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64]
+    widths = [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64]  # both width lists
     steps = sorted({v for w in widths for v in (32 * w - 1, 32 * w, 32 * w + 1) if 1 <= v <= 2048} | {1, 2, 3})
     steps = np.array(steps, dtype=np.int32)
     o = W.binomial_options(len(steps), seed=41)

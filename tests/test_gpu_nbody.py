@@ -199,9 +199,12 @@ def test_fd_kernel_matches_oracle_and_adjoint(E, oracle_mod):
     eng.work_items(64, 1).scheduler("dynamic", (16,)).program(p).run().synchronize()
     got = out.cpu().numpy()
     ref = oracle_mod.nbody_fd_energy_grad(pos, EPS2, body, comp, h)
-    # FP32 pair terms in FP64 sums: row error ~ sqrt(n) eps |phi|, divided by 2h
-    scale = np.abs(ref) + 1e-4 * n
-    assert (np.abs(got - ref) / scale).max() <= 1e-4
+    # FP32 pair terms in FP64 sums: each term m_j phi_j carries ~3e-7 relative
+    # rounding (difference, squares, rsqrt), so a row of n terms errs by
+    # ~sqrt(n) * 3e-7 * rms(phi) (~2e-5 at n = 4096, rms(phi) ~ 1) and the
+    # difference of two rows divided by 2h = 2e-3 by ~0.03; allow 3x, plus
+    # 2e-3 relative
+    assert (np.abs(got - ref) <= 2e-3 * np.abs(ref) + 0.1).all(), np.abs(got - ref).max()
     # against the analytic gradient (FD truncation O(h^2) dominates near close pairs)
     grad = oracle_mod.nbody_energy_grad(pos, EPS2)
     gi = np.array([grad[b, c] for b, c in zip(body, comp)])
