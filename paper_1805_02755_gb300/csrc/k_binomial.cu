@@ -61,13 +61,12 @@ struct Lat {
 // Going from width R to the next width R' happens when the live nodes fit in
 // 32 R'.  Price only: steps of about 1/8 (~91% of the computed slots live for
 // depths U{256..2048}).  With greeks every slot costs 10 instructions instead
-// of 3, so the unrolled level code of many widths would overflow the
-// instruction cache; a shorter list keeps ~82% live at 2/5 of the code.
+// of 3 and the unrolled level code of many widths starves on instruction
+// fetch; halving widths keep ~70% of the slots live with the least code.
 template <bool G>
 __host__ __device__ constexpr int width_at(int i)
 {
-    return G ? (i == 0 ? 64 : i == 1 ? 48 : i == 2 ? 32 : i == 3 ? 24 : i == 4 ? 16 : i == 5 ? 8 : i == 6 ? 4
-              : i == 7 ? 2 : i == 8 ? 1 : 0)
+    return G ? (i == 0 ? 64 : i == 1 ? 32 : i == 2 ? 16 : i == 3 ? 8 : i == 4 ? 4 : i == 5 ? 2 : i == 6 ? 1 : 0)
              : (i == 0 ? 64 : i == 1 ? 56 : i == 2 ? 48 : i == 3 ? 40 : i == 4 ? 32 : i == 5 ? 28 : i == 6 ? 24
               : i == 7 ? 20 : i == 8 ? 16 : i == 9 ? 14 : i == 10 ? 12 : i == 11 ? 10 : i == 12 ? 8 : i == 13 ? 7
               : i == 14 ? 6 : i == 15 ? 5 : i == 16 ? 4 : i == 17 ? 3 : i == 18 ? 2 : i == 19 ? 1 : 0);

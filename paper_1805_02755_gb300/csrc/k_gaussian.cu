@@ -157,6 +157,7 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
 }
 
 struct Gauss31Body {
+    static constexpr uint32_t kThreads = kBlock;
     using Params = GaussParams;
     Params p;
     float (*st)[kSW];  // [kNIN][kSW] staged input, then [kRB][kSW] vertical results
@@ -199,7 +200,7 @@ struct Gauss31Body {
     {
         const ChunkGeom g = geom(p, off, len, t);
         stage(g);
-        __syncthreads();
+        body_sync(kBlock);
         // vertical pass: staged column c <-> image column x0 - 16 + c, one column per thread
         float acc[kRB];
         const int c1 = threadIdx.x;
@@ -212,13 +213,13 @@ struct Gauss31Body {
             for (int o = 0; o < kRB; ++o)
                 if (k - o >= 0 && k - o < 31) acc[o] = fmaf(wr[k - o], v, acc[o]);
         }
-        __syncthreads();  // every staged row has been read
+        body_sync(kBlock);  // every staged row has been read
 #pragma unroll
         for (int o = 0; o < kRB; ++o) st[o][c1] = acc[o];
-        __syncthreads();
+        body_sync(kBlock);
         // horizontal pass: output x needs vertical results at staged columns x - x0 + 1 .. + 31
         horizontal_store<31, kSW, 16>(p, g, &st[0][0], wr, nullptr);
-        __syncthreads();
+        body_sync(kBlock);
     }
 };
 
@@ -227,6 +228,7 @@ struct Gauss31Body {
 constexpr int kSWA = kTW + 64;
 
 struct GaussAnyBody {
+    static constexpr uint32_t kThreads = kBlock;
     using Params = GaussParams;
     Params p;
     float *sv;  // [kRB][kSWA]
@@ -253,13 +255,13 @@ struct GaussAnyBody {
                 sv[o * kSWA + col] = acc;
             }
         }
-        __syncthreads();
+        body_sync(kBlock);
         horizontal_store<0, kSWA, 31>(p, g, sv, nullptr, wsh);
-        __syncthreads();
+        body_sync(kBlock);
     }
 };
 
-__global__ void __launch_bounds__(kBlock, 3) k_gauss31(GaussParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock + 32, 3) k_gauss31(GaussParams prm, SchedArgs s)
 {
     extern __shared__ __align__(16) float smem_g[];
     Gauss31Body b;
@@ -267,10 +269,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_gauss31(GaussParams prm, SchedArg
     b.st = reinterpret_cast<float(*)[kSW]>(smem_g);
 #pragma unroll
     for (int u = 0; u < 31; ++u) b.wr[u] = __ldg(prm.w + u);
-    drive(s, b);
+    drive_ws(s, b);
 }
 
-__global__ void __launch_bounds__(kBlock) k_gauss_any(GaussParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock + 32) k_gauss_any(GaussParams prm, SchedArgs s)
 {
     __shared__ __align__(16) float sv[kRB][kSWA];
     __shared__ float wsh[kMaxTaps];
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kBlock) k_gauss_any(GaussParams prm, SchedArgs
     b.p = prm;
     b.sv = &sv[0][0];
     b.wsh = wsh;
-    drive(s, b);
+    drive_ws(s, b);
 }
 
 GaussParams params_of(const KArgs &a, uint32_t lws)
@@ -354,7 +356,7 @@ int ctas_per_sm()
 {
     if (!set_smem_attr()) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gauss31, kBlock, kSmem31) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gauss31, kBlock + 32, kSmem31) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -369,11 +371,11 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
             err = "cannot raise the shared-memory limit";
             return ECL_ERR_CUDA;
         }
-        k_gauss31<<<c.grid, kBlock, kSmem31, c.stream>>>(p, s);
+        k_gauss31<<<c.grid, kBlock + 32, kSmem31, c.stream>>>(p, s);
     } else {
         // the generic path keeps a smaller resident count; the plan used the fast path's
         // count, so it is clamped here: more CTAs than resident is still correct
-        k_gauss_any<<<c.grid, kBlock, 0, c.stream>>>(p, s);
+        k_gauss_any<<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
@@ -392,7 +394,7 @@ extern const KernelDesc kGaussian = {
      {"taps", A_I32}},
     1,
     1,
-    kBlock,
+    kBlock + 32,
     0,
     validate,
     grain,

@@ -6,8 +6,9 @@
 // evaluation bit for bit.
 //
 // Work-item g computes pixels 4g .. 4g+3 of the row-major image and writes
-// them with one 128-bit store.  One chunk = one work-group; the CTA (256
-// threads) strides over the work-group's work-items.  The four pixels of a
+// them with one 128-bit store.  One chunk = one work-group; the CTA's 256
+// compute threads stride over the work-group's work-items (plus one warp
+// that claims chunks ahead).  The four pixels of a
 // thread iterate interleaved so that four independent dependency chains
 // are in flight.
 #include <cuda_runtime.h>
@@ -21,6 +22,7 @@ namespace {
 constexpr int kBlock = 256;
 
 struct MandelbrotBody {
+    static constexpr uint32_t kThreads = kBlock;
     struct Params {
         uint32_t *out;
         int64_t W, H;
@@ -40,7 +42,7 @@ struct MandelbrotBody {
         const uint64_t npx = (uint64_t)p.W * (uint64_t)p.H;
         const uint64_t wg = off + t;
         const uint64_t wi_end = (wg + 1) * p.lws;
-        for (uint64_t wi = wg * p.lws + threadIdx.x; wi < wi_end; wi += blockDim.x) {
+        for (uint64_t wi = wg * p.lws + threadIdx.x; wi < wi_end; wi += kBlock) {
             const uint64_t px0 = wi * 4;
             if (px0 >= npx) break;
             float cx[4], cy[4], x[4], y[4];
@@ -84,10 +86,10 @@ struct MandelbrotBody {
     }
 };
 
-__global__ void __launch_bounds__(kBlock) k_mandelbrot(MandelbrotBody::Params prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock + 32) k_mandelbrot(MandelbrotBody::Params prm, SchedArgs s)
 {
     MandelbrotBody b{prm};
-    drive(s, b);
+    drive_ws(s, b);
 }
 
 MandelbrotBody::Params params_of(const KArgs &a, uint32_t lws)
@@ -146,7 +148,7 @@ uint32_t nchunks(const KArgs &a, uint64_t, uint32_t lws, uint64_t off, uint64_t 
 int ctas_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mandelbrot, kBlock, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mandelbrot, kBlock + 32, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -155,7 +157,7 @@ int ctas_per_sm()
 
 ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
-    k_mandelbrot<<<c.grid, kBlock, 0, c.stream>>>(params_of(a, c.lws), s);
+    k_mandelbrot<<<c.grid, kBlock + 32, 0, c.stream>>>(params_of(a, c.lws), s);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);
@@ -173,7 +175,7 @@ extern const KernelDesc kMandelbrot = {
      {"dx", A_F32}, {"dy", A_F32}, {"max_iter", A_I32}},
     4,
     1,
-    kBlock,
+    kBlock + 32,
     0,
     validate,
     grain,

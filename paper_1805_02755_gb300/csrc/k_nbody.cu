@@ -103,6 +103,7 @@ __device__ __forceinline__ void stage_tile2(float4 *shxy, float4 *shzm, const fl
 //   s = (m_j inv)(inv inv), a += s d.
 template <uint32_t MODE>
 struct ForceBody {
+    static constexpr uint32_t kThreads = kBlock;
     using Params = NBodyParams;
     Params p;
     float4 *shxy, *shzm;  // [kTile] duplicated j-bodies
@@ -128,9 +129,9 @@ struct ForceBody {
         f2 AX = 0, AY = 0, AZ = 0, POT = 0;
         const int64_t ntiles = (p.n + kTile - 1) / kTile;
         for (int64_t tile = 0; tile < ntiles; ++tile) {
-            __syncthreads();
+            body_sync(kBlock);
             stage_tile2(shxy, shzm, p.pos, p.n, tile);
-            __syncthreads();
+            body_sync(kBlock);
             f2 TX = 0, TY = 0, TZ = 0, TP = 0;
             const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + s * span);
             const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + s * span);
@@ -160,10 +161,10 @@ struct ForceBody {
         upk(AY, ay0, ay1);
         upk(AZ, az0, az1);
         upk(POT, pt0, pt1);
-        __syncthreads();
+        body_sync(kBlock);
         red[threadIdx.x] = make_float4(ax0, ay0, az0, pt0);
         red[kBlock + threadIdx.x] = make_float4(ax1, ay1, az1, pt1);
-        __syncthreads();
+        body_sync(kBlock);
         if (s < 2) {  // slice-0 thread finishes body b, slice-1 thread body b + half
             const int64_t i = s == 0 ? i0 : i1;
             if (i < p.n) {
@@ -218,6 +219,7 @@ __device__ __forceinline__ double warp_sum_d(double v)
 }
 
 struct EnergyBody {
+    static constexpr uint32_t kThreads = kBlock;
     using Params = EnergyParams;
     Params p;
     float4 *sh;
@@ -249,9 +251,9 @@ struct EnergyBody {
         const int64_t tfirst = i0 / kTile, nt = ntiles - tfirst;
         const int64_t ta = tfirst + nt * seg / kESeg, tb = tfirst + nt * (seg + 1) / kESeg;
         for (int64_t tile = ta; tile < tb; ++tile) {
-            __syncthreads();
+            body_sync(kBlock);
             stage_tile(sh, p.pos, p.n, tile);
-            __syncthreads();
+            body_sync(kBlock);
             float tp = 0.f;
             const int64_t j0 = tile * kTile + s * span;
             const float4 *q = sh + s * span;
@@ -279,9 +281,9 @@ struct EnergyBody {
         // this thread's share of -m_i sum_{j>i} m_j phi_ij, reduced in a fixed order
         double v = valid ? -(double)pi.w * e : 0.0;
         v = warp_sum_d(v);
-        __syncthreads();
+        body_sync(kBlock);
         if ((threadIdx.x & 31) == 0) dsh[threadIdx.x / 32] = v;
-        __syncthreads();
+        body_sync(kBlock);
         if (threadIdx.x == 0) {
             double w = 0.0;
             for (int q = 0; q < kBlock / 32; ++q) w += dsh[q];
@@ -290,7 +292,7 @@ struct EnergyBody {
             const unsigned before = atomicAdd(p.counter, 1u);
             dsh[0] = (before + 1 == (unsigned)(p.G * kESeg)) ? 1.0 : 0.0;
         }
-        __syncthreads();
+        body_sync(kBlock);
         if (dsh[0] != 0.0) {  // last chunk of the run: sum the partials in order
             __threadfence();
             double acc = 0.0;
@@ -299,10 +301,10 @@ struct EnergyBody {
             const uint64_t a = threadIdx.x * per;
             const uint64_t z = min(np, a + per);
             for (uint64_t w = a; w < z; ++w) acc += *((volatile double *)p.partial + w);
-            __syncthreads();
+            body_sync(kBlock);
             __shared__ double tree[kBlock];
             tree[threadIdx.x] = acc;
-            __syncthreads();
+            body_sync(kBlock);
             if (threadIdx.x == 0) {
                 double tot = 0.0;
                 for (int q = 0; q < kBlock; ++q) tot += tree[q];
@@ -310,7 +312,7 @@ struct EnergyBody {
                 *p.counter = 0u;
             }
         }
-        __syncthreads();
+        body_sync(kBlock);
     }
 };
 
@@ -325,6 +327,7 @@ struct FDParams {
 };
 
 struct FDBody {
+    static constexpr uint32_t kThreads = kBlock;
     using Params = FDParams;
     Params p;
     double *dsh;  // [2 * kBlock / 32]
@@ -368,12 +371,12 @@ struct FDBody {
         }
         rp = warp_sum_d(rp);
         rm = warp_sum_d(rm);
-        __syncthreads();
+        body_sync(kBlock);
         if ((threadIdx.x & 31) == 0) {
             dsh[threadIdx.x / 32] = rp;
             dsh[kBlock / 32 + threadIdx.x / 32] = rm;
         }
-        __syncthreads();
+        body_sync(kBlock);
         if (threadIdx.x == 0) {
             double a = 0.0, z = 0.0;
             for (int q = 0; q < kBlock / 32; ++q) {
@@ -382,13 +385,13 @@ struct FDBody {
             }
             p.out[smp] = -(double)pi.w * (a - z) / ((double)xp - (double)xm);
         }
-        __syncthreads();
+        body_sync(kBlock);
     }
 };
 
 // ---------------------------------------------------------------- kernels
 template <uint32_t MODE>
-__global__ void __launch_bounds__(kBlock) k_nbody_force(NBodyParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock + 32, 3) k_nbody_force(NBodyParams prm, SchedArgs s)
 {
     __shared__ __align__(16) float4 shxy[kTile];
     __shared__ __align__(16) float4 shzm[kTile];
@@ -398,10 +401,10 @@ __global__ void __launch_bounds__(kBlock) k_nbody_force(NBodyParams prm, SchedAr
     b.shxy = shxy;
     b.shzm = shzm;
     b.red = red;
-    drive(s, b);
+    drive_ws(s, b);
 }
 
-__global__ void __launch_bounds__(kBlock) k_nbody_energy(EnergyParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock + 32) k_nbody_energy(EnergyParams prm, SchedArgs s)
 {
     __shared__ float4 sh[kTile];
     __shared__ double dsh[kBlock / 32];
@@ -409,22 +412,22 @@ __global__ void __launch_bounds__(kBlock) k_nbody_energy(EnergyParams prm, Sched
     b.p = prm;
     b.sh = sh;
     b.dsh = dsh;
-    drive(s, b);
+    drive_ws(s, b);
 }
 
-__global__ void __launch_bounds__(kBlock) k_nbody_fd(FDParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock + 32) k_nbody_fd(FDParams prm, SchedArgs s)
 {
     __shared__ double dsh[2 * kBlock / 32];
     FDBody b;
     b.p = prm;
     b.dsh = dsh;
-    drive(s, b);
+    drive_ws(s, b);
 }
 
 int occ(const void *fn)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock + 32, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -497,7 +500,7 @@ ecl_status l_step(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.out_pos = a.buf<float4>(5);
     p.out_vel = a.buf<float4>(6);
     p.lws = c.lws;
-    k_nbody_force<NB_STEP><<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    k_nbody_force<NB_STEP><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
 
@@ -523,7 +526,7 @@ ecl_status l_acc(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.eps2 = a.f32(2);
     p.out_acc = a.buf<float4>(3);
     p.lws = c.lws;
-    k_nbody_force<NB_ACC><<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    k_nbody_force<NB_ACC><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
 
@@ -554,7 +557,7 @@ ecl_status l_adj(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.grad_E = a.buf<const float>(3);
     p.out_grad = a.buf<float4>(4);
     p.lws = c.lws;
-    k_nbody_force<NB_ADJ><<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    k_nbody_force<NB_ADJ><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
 
@@ -590,7 +593,7 @@ ecl_status l_energy(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std:
     p.partial = (double *)(ws + 256);
     p.G = G;
     p.lws = c.lws;
-    k_nbody_energy<<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    k_nbody_energy<<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
 
@@ -630,7 +633,7 @@ ecl_status l_fd(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::str
     p.comp = a.buf<const int>(5);
     p.count = a.i32(6);
     p.out = a.buf<double>(7);
-    k_nbody_fd<<<c.grid, kBlock, 0, c.stream>>>(p, s);
+    k_nbody_fd<<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
 
@@ -642,33 +645,33 @@ extern const KernelDesc kNBody = {
     "nbody", 7,
     {{"in_pos", A_BUF_IN}, {"in_vel", A_BUF_IN}, {"bodies", A_I32}, {"del_t", A_F32}, {"esp_sqr", A_F32},
      {"out_pos", A_BUF_OUT}, {"out_vel", A_BUF_OUT}},
-    1, 1, kBlock, 0, v_step, grain1, nchunks_wg, o_step, l_step,
+    1, 1, kBlock + 32, 0, v_step, grain1, nchunks_wg, o_step, l_step,
 };
 
 extern const KernelDesc kNBodyAcc = {
     "nbody_acc", 4,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_acc", A_BUF_OUT}},
-    1, 1, kBlock, 0, v_acc, grain1, nchunks_wg, o_acc, l_acc,
+    1, 1, kBlock + 32, 0, v_acc, grain1, nchunks_wg, o_acc, l_acc,
 };
 
 extern const KernelDesc kNBodyAdjoint = {
     "nbody_adjoint", 5,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"grad_E", A_BUF_IN},
      {"out_grad", A_BUF_OUT}},
-    1, 1, kBlock, 0, v_adj, grain1, nchunks_wg, o_adj, l_adj,
+    1, 1, kBlock + 32, 0, v_adj, grain1, nchunks_wg, o_adj, l_adj,
 };
 
 extern const KernelDesc kNBodyEnergy = {
     "nbody_energy", 4,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_energy", A_BUF_OUT}},
-    1, 0, kBlock, 0, v_energy, grain1, nchunks_energy, o_energy, l_energy,
+    1, 0, kBlock + 32, 0, v_energy, grain1, nchunks_energy, o_energy, l_energy,
 };
 
 extern const KernelDesc kNBodyFD = {
     "nbody_fd", 8,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"h", A_F32}, {"body", A_BUF_IN},
      {"comp", A_BUF_IN}, {"count", A_I32}, {"out", A_BUF_OUT}},
-    1, 1, kBlock, 0, v_fd, grain1, nchunks_wg, o_fd, l_fd,
+    1, 1, kBlock + 32, 0, v_fd, grain1, nchunks_wg, o_fd, l_fd,
 };
 
 }  // namespace ecl

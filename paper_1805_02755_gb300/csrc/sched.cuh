@@ -194,6 +194,18 @@ __device__ __forceinline__ bool finish_chunks(const SchedArgs &s, uint32_t pkg, 
     return finished;
 }
 
+// The same accounting without waiting for an atomic's result: t1 becomes
+// the latest chunk end (a reduction the CTA does not wait for).  Used when
+// no coverage is requested, so nobody needs to know which CTA finished the
+// package.
+__device__ __forceinline__ void finish_chunks_async(const SchedArgs &s, uint32_t pkg, uint64_t te)
+{
+    if (s.C == 1)
+        s.rec[pkg].t1 = te;
+    else
+        atomicMax((unsigned long long *)&s.rec[pkg].t1, (unsigned long long)te);
+}
+
 // End of a persistent CTA (all threads call it): writes the per-CTA record,
 // and the last CTA to leave puts the queue back to its initial state.
 __device__ __forceinline__ void exit_protocol(const SchedArgs &s, uint32_t d, uint64_t t_first, uint64_t t_last,
@@ -274,6 +286,132 @@ __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
         }
     }
     exit_protocol(s, d, t_first, t_last, busy, nchunks_done, &sc.last);
+}
+
+// ------------------------------------------------------------------ mbarrier helpers
+__device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void sbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void sbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sh_addr(bar)) : "memory");
+}
+
+// Bounded wait on phase `parity`; false (and the queue's error word set)
+// when it gave up after about two seconds.
+__device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsigned int *gerr)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(sh_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 63u) == 0) {
+            const uint64_t now = gtime();
+            if (!t0) t0 = now;
+            if (now - t0 > 2000000000ull) {
+                atomicExch(gerr, (unsigned int)ECL_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Barrier among the compute warps only (warp-specialised driver).
+__device__ __forceinline__ void body_sync(uint32_t nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Warp-specialised persistent driver: the CTA has Body::kThreads compute
+// threads plus one scheduler warp.  The scheduler warp claims chunks into a
+// two-slot ring ahead of the compute warps, so the atomic round trips of a
+// claim (and a device's election to fetch its next package) overlap the
+// previous chunk's work.  Bodies synchronise with body_sync(kThreads), never
+// __syncthreads.  Every wait is bounded; a wait that gives up sets the queue's
+// error word and ends the CTA's work.
+template <class Body>
+__device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
+{
+    constexpr uint32_t NC = Body::kThreads;
+    __shared__ Claim ring[2];
+    __shared__ uint64_t full[2], empty[2];
+    __shared__ uint32_t flag;
+    if (s.mode == MODE_MONO) {  // the whole range is one package, CTA b = chunk b
+        if (threadIdx.x < NC) body.run(0, s.G, blockIdx.x, s.mono_nchunks);
+        return;
+    }
+    unsigned int *gerr = &s.q->error;
+    const uint32_t d = blockIdx.x / s.C;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            sbar_init(&full[i], 1);
+            sbar_init(&empty[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint64_t t_first = 0, t_last = 0, busy = 0;
+    uint32_t nchunks_done = 0;
+    if (threadIdx.x >= NC) {
+        if (threadIdx.x == NC) {  // scheduler: lane 0 of the last warp
+            for (uint32_t i = 0;; ++i) {
+                const uint32_t r = i & 1;
+                if (!sbar_wait(&empty[r], ((i >> 1) & 1) ^ 1, gerr)) break;
+                Claim c = (*(volatile unsigned int *)gerr) ? Claim{} : claim_chunks<Body>(s, body.p, d);
+                if (*(volatile unsigned int *)gerr) c.done = 1;
+                ring[r] = c;
+                sbar_arrive(&full[r]);
+                if (c.done) break;
+            }
+        }
+    } else {
+        for (uint32_t i = 0;; ++i) {
+            const uint32_t r = i & 1;
+            if (threadIdx.x == 0) flag = sbar_wait(&full[r], (i >> 1) & 1, gerr) ? 0u : 1u;
+            body_sync(NC);
+            if (flag) break;
+            const Claim c = ring[r];
+            if (c.done) break;
+            uint64_t ts = 0;
+            if (threadIdx.x == 0) ts = gtime();
+            for (uint32_t t = c.t_begin; t < c.t_end; ++t) body.run(c.off, c.len, t, c.nchunks);
+            body_sync(NC);  // all compute threads are done with the chunk and the slot
+            if (threadIdx.x == 0) {
+                sbar_arrive(&empty[r]);
+                const uint64_t te = gtime();
+                if (!t_first) t_first = ts;
+                t_last = te;
+                busy += te - ts;
+                nchunks_done += c.t_end - c.t_begin;
+                if (!s.coverage) {
+                    finish_chunks_async(s, c.pkg, te);
+                    flag = 0;
+                } else {
+                    flag = finish_chunks(s, c.pkg, c.t_end - c.t_begin, c.nchunks, te) ? 1u : 0u;
+                }
+            }
+            if (s.coverage) {  // debug: count every work-group of a finished package
+                body_sync(NC);
+                if (flag)
+                    for (uint64_t w = c.off + threadIdx.x; w < c.off + c.len; w += NC) atomicAdd(&s.coverage[w], 1u);
+                body_sync(NC);
+                if (threadIdx.x == 0) flag = 0;
+            }
+        }
+    }
+    __syncthreads();
+    exit_protocol(s, d, t_first, t_last, busy, nchunks_done, &flag);
 }
 
 }  // namespace ecl
