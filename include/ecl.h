@@ -245,6 +245,34 @@ ecl_status ecl_kernel_arg(const char *kernel_name, int index, int *kind, const c
 int ecl_kernel_count(void);
 const char *ecl_kernel_name(int i);
 
+/* ---------------------------------------------------------------- no allocation
+ * Potential energy E = -sum_{i<j} m_i m_j / sqrt(|r_ij|^2 + eps2) of n bodies
+ * without allocating any memory.  The paper has no counterpart to this call:
+ * it exists for callers that must not call cudaMalloc, such as a process
+ * whose device memory is entirely owned by another allocator (a framework
+ * pool, a memory-capped serving process) where an allocation behind its back
+ * would fail or be counted against it.  The computation is that of the
+ * "nbody_energy" program (same kernel, FP32 pair terms, FP64 sums, same
+ * result) run as one plain launch without the package queue, so no engine
+ * is needed.
+ *   pos4        device float4[n] (x, y, z, m), 16-byte aligned
+ *   n           1 .. 524288 bodies (ECL_ERR_SIZE beyond: the scratch holds
+ *               one FP64 partial per 8 x 64 bodies, 512 KiB in all)
+ *   eps2        softening, squared
+ *   out_energy  device double[1], 8-byte aligned
+ *   cuda_stream stream the work is ordered on (NULL = legacy default)
+ * The scratch is a fixed array in the library's device image: every GPU that
+ * loads the library holds it (512 KiB + 256 B) until the process exits.  The
+ * first call on a device looks its address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the one array and each call clears its
+ * counter first, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race: order them on one stream.  Asynchronous like
+ * ecl_run; errors: ECL_ERR_ARG (NULL or misaligned pointer, n <= 0),
+ * ECL_ERR_SIZE, ECL_ERR_CUDA. */
+ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, double *out_energy,
+                                    void *cuda_stream);
+
 /* ---------------------------------------------------------------- kernels
  * Built-in kernels and their arguments, in order (B = buffer, S = scalar).
  *

@@ -90,6 +90,7 @@ def lib():
             "ecl_program_local": (_st, [_vp, ctypes.c_int, ctypes.c_size_t]),
             "ecl_kernel_arg": (_st, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_char_p)]),
+            "ecl_nbody_energy_noalloc": (_st, [_vp, ctypes.c_int32, ctypes.c_float, _vp, _vp]),
             "ecl_kernel_count": (ctypes.c_int, []),
             "ecl_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
         }
@@ -285,6 +286,13 @@ def ecl_kernel_arg(kernel_name: str, index: int):
     if st != ECL_OK:
         return None
     return kind.value, name.value.decode()
+
+
+def ecl_nbody_energy_noalloc(pos4, n: int, eps2: float, out_energy, cuda_stream=None) -> None:
+    """Potential energy into out_energy (device double[1]) without allocating;
+    see include/ecl.h for the limits (n <= 524288, one shared scratch array)."""
+    _check(lib().ecl_nbody_energy_noalloc(_vp(pos4.data_ptr()), n, eps2, _vp(out_energy.data_ptr()),
+                                          _vp(_stream_handle(cuda_stream))))
 
 
 def ecl_kernel_count() -> int:

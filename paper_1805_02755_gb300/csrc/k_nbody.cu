@@ -20,6 +20,8 @@
 // FP64, reduced in a fixed order, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ecl_internal.h"
 #include "sched.cuh"
 
@@ -674,4 +676,73 @@ extern const KernelDesc kNBodyFD = {
     1, 1, kBlock + 32, 0, v_fd, grain1, nchunks_wg, o_fd, l_fd,
 };
 
+// ---------------------------------------------------------------- energy without allocation
+// Scratch of ecl_nbody_energy_noalloc: a 256-byte header (the chunk counter)
+// followed by one FP64 partial per (work-group, segment).  It lives in every
+// GPU that loads this library, for the life of the process.
+namespace {
+constexpr uint64_t kNoAllocPartials = 1u << 16;  // 512 KiB of FP64 partials
+constexpr uint32_t kNoAllocLws = 64;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_energy_scratch[256 + kNoAllocPartials * sizeof(double)];
+
+namespace {
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[kNoAllocMaxDevices];
+}  // namespace
+
 }  // namespace ecl
+
+extern "C" ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, double *out_energy,
+                                               void *cuda_stream)
+{
+    using namespace ecl;
+    if (!pos4 || !out_energy || n <= 0 || (uintptr_t)pos4 % 16 || (uintptr_t)out_energy % 8) return ECL_ERR_ARG;
+    const uint64_t G = ((uint64_t)n + kNoAllocLws - 1) / kNoAllocLws;
+    if (G * kESeg > kNoAllocPartials) return ECL_ERR_SIZE;  // more than 524288 bodies
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return ECL_ERR_CUDA;
+    }
+    void *scratch = nullptr;
+    {
+        // once per device, with that device current: the scratch array's device address
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_energy_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return ECL_ERR_CUDA;
+            }
+            g_scratch_ptr[dev] = ptr;
+        }
+        scratch = g_scratch_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the chunk counter must start at zero (a previous call that failed may have left it set)
+    if (cudaMemsetAsync(scratch, 0, 256, st) != cudaSuccess) {
+        cudaGetLastError();
+        return ECL_ERR_CUDA;
+    }
+    EnergyParams p{};
+    p.pos = (const float4 *)pos4;
+    p.n = n;
+    p.eps2 = eps2;
+    p.out_E = out_energy;
+    p.counter = (unsigned *)scratch;
+    p.partial = (double *)((char *)scratch + 256);
+    p.G = G;
+    p.lws = kNoAllocLws;
+    SchedArgs s{};  // a monolithic launch: no package queue, so no engine memory either
+    s.mode = MODE_MONO;
+    s.G = G;
+    s.grain = 1;
+    s.units = G;
+    s.mono_nchunks = (uint32_t)(G * kESeg);
+    k_nbody_energy<<<(unsigned)(G * kESeg), kBlock + 32, 0, st>>>(p, s);
+    if (cudaGetLastError() != cudaSuccess) return ECL_ERR_CUDA;
+    return ECL_OK;
+}
