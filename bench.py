@@ -54,11 +54,6 @@ def load_peaks():
                 src="fallback")
 
 
-def fp32_peak_tflops(sms, mhz):
-    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA, at the given SM clock."""
-    return sms * 128 * 2 * mhz * 1e6 / 1e12
-
-
 # ====================================================================== workloads
 class Workload:
     name = ""
@@ -123,10 +118,10 @@ class Mandelbrot(Workload):
                                                           r["dx"], r["dy"], r["max_iter"])
 
     def after(self):
-        # algorithmic work: 8 FP32 operations per iteration (x^2, y^2, |z|^2, x^2-y^2, +cx, 2x, *y, +cy)
+        # algorithmic work: 8 FP32 instructions per iteration (x^2, y^2, |z|^2, x^2-y^2, +cx, 2x, *y, +cy)
         its = int(self.d_out[0].to(self.torch.int64).sum().item())
         self.iterations = its
-        return dict(bound="alu", flops=8.0 * its, unit_name="pixels/s", units=self.npx)
+        return dict(bound="alu", inst=8.0 * its, flops=8.0 * its, unit_name="pixels/s", units=self.npx)
 
     def cpu_sample(self, O, threads):
         r = self.r
@@ -165,7 +160,8 @@ class Gaussian(Workload):
     def after(self):
         # algorithmic: 62 FMAs per pixel (31 vertical + 31 horizontal), 8 bytes of HBM per pixel
         npx = self.H * self.Wd
-        return dict(bound="alu", flops=2.0 * 62 * npx, bytes=8.0 * npx, unit_name="pixels/s", units=npx)
+        return dict(bound="alu", inst=62.0 * npx, flops=2.0 * 62 * npx, bytes=8.0 * npx, unit_name="pixels/s",
+                    units=npx)
 
     def cpu_sample(self, O, threads):
         t = time.perf_counter()
@@ -226,16 +222,19 @@ class NBody(Workload):
 
     def alg(self, name):
         n = self.n
-        # FP32 flops per pair, FMA counted as 2: force 18 (3 sub, 3 FMA, 3 mul, 3 FMA),
-        # energy 10 over i<j (3 sub, 3 FMA, 1 FMA), adjoint 19 (force + potential add),
-        # finite differences 2 x 9 per j for each sample
+        # FP32 pipe instructions per pair (flops with FMA = 2 in brackets): force 12 [18]
+        # (3 sub, 3 FMA, 3 mul, 3 FMA) + 1 rsqrt; energy 7 [10] over i<j (3 sub, 3 FMA,
+        # 1 FMA) + 1 rsqrt, which makes it bound by the 16/clk rsqrt unit; adjoint 13 [19];
+        # finite differences 2 x 8 per j for each sample
         if name == "nbody_acc":
-            return dict(bound="alu", flops=18.0 * n * n, unit_name="interactions/s", units=n * n)
+            return dict(bound="alu", inst=12.0 * n * n, flops=18.0 * n * n, unit_name="interactions/s", units=n * n)
         if name == "nbody_energy":
-            return dict(bound="alu", flops=10.0 * n * (n - 1) / 2, unit_name="pairs/s", units=n * (n - 1) // 2)
+            pairs = n * (n - 1) / 2
+            return dict(bound="mufu", inst=pairs, flops=10.0 * pairs, unit_name="pairs/s", units=int(pairs))
         if name == "nbody_adjoint":
-            return dict(bound="alu", flops=19.0 * n * n, unit_name="interactions/s", units=n * n)
-        return dict(bound="alu", flops=18.0 * n * self.NFD, unit_name="samples/s", units=self.NFD)
+            return dict(bound="alu", inst=13.0 * n * n, flops=19.0 * n * n, unit_name="interactions/s", units=n * n)
+        return dict(bound="alu", inst=16.0 * n * self.NFD, flops=18.0 * n * self.NFD, unit_name="samples/s",
+                    units=self.NFD)
 
     def cpu_sample(self, O, threads):
         nb = 2048
@@ -293,10 +292,52 @@ class Binomial(Workload):
         eng.program(self.program(self.d_in, self.d_out, greeks=False))
         return eng
 
+    def batched_report(self, timed):
+        """The same options as 64 batches of uneven size: 64 launches (plain)
+        against one batched launch, and that launch replayed from a CUDA graph."""
+        from paper_1805_02755_gb300.batching import BinomialBatch, capture_graph, split_uneven
+        E = self.E
+        S, K, T, sig, st = self.d_in
+        price, gr = self.d_out
+        sizes = split_uneven(self.n, 64, seed=11)
+        batches, engines = [], []
+        o = 0
+        sch, prm, D, C = self.sched
+        for n in sizes:
+            sl = slice(o, o + n)
+            b = dict(S=S[sl], K=K[sl], T=T[sl], sigma=sig[sl], steps=st[sl], r=self.o["r"], price=price[sl],
+                      greeks=gr[sl])
+            batches.append(b)
+            eng = E.Engine(0)
+            p = E.Program("binomial")
+            for t in (b["S"], b["K"], b["T"], b["sigma"], b["steps"]):
+                p.in_(t)
+            p.out(b["price"]).out(b["greeks"])
+            p.args(b["S"], b["K"], b["T"], b["sigma"], b["steps"], self.o["r"], n, b["price"], b["greeks"])
+            eng.work_items(n * 32, 32).scheduler(sch, prm).workers(D, C).program(p)
+            engines.append(eng)
+            o += n
+
+        def plain():
+            for e in engines:
+                e.run()
+        ms_plain = timed(plain, 2)
+        bb = BinomialBatch(batches, with_greeks=True, scheduler=(sch, prm), workers=(D, C))
+        ms_batched = timed(bb.run, 2)
+        g = capture_graph(bb.engine)
+        ms_graph = timed(g.replay, 2)
+        for e in engines:
+            e.close()
+        bb.close()
+        return dict(batches=len(sizes), largest=max(sizes), smallest=min(sizes), ms_64_launches=ms_plain,
+                    ms_one_batched_launch=ms_batched, ms_batched_graph_replay=ms_graph,
+                    batched_over_plain=ms_batched / ms_plain)
+
     def after(self):
-        # FP32 flops per node update: price 4 (add, sub, FMA), delta 4, vega 6
-        return dict(bound="alu", flops=14.0 * self.nodes, unit_name="options/s", units=self.n,
-                    extra={"node_updates_per_s": self.nodes})
+        # FP32 instructions per node update: price 3 (add, sub, FMA), delta 3, vega 4
+        # (flops with FMA = 2: 4 + 4 + 6)
+        return dict(bound="alu", inst=10.0 * self.nodes, flops=14.0 * self.nodes, unit_name="options/s",
+                    units=self.n, extra={"node_updates_per_s": self.nodes})
 
     def cpu_sample(self, O, threads):
         t = time.perf_counter()
@@ -585,16 +626,22 @@ def run_ours(args):
         d[alg["unit_name"]] = alg["units"] / (ms * 1e-3)
         for k2, v2 in alg.get("extra", {}).items():
             d[k2] = v2 / (ms * 1e-3)
+        if hasattr(w, "batched_report") and not args.no_batched:
+            d["batched"] = w.batched_report(timed)
         if hasattr(w, "plain_engine"):  # the plain form beside the adjoint form
             pe = w.plain_engine()
             ms_plain = timed(pe.run, max(3, min(args.steps, 5)))
             d["plain_ms"] = ms_plain
             d["adjoint_over_plain"] = ms / ms_plain
             pe.close()
-        if alg["bound"] == "alu":
-            peak = fp32_peak_tflops(sms, peaks["sm_max_mhz"])
-            ach = alg["flops"] / (ms * 1e-3) / 1e12
-            d["roofline"] = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak)
+        if alg["bound"] in ("alu", "mufu"):
+            # FP32 pipe: 128 lanes per SM; rsqrt unit: 16 per SM; per clock at the max SM clock
+            lanes = 128 if alg["bound"] == "alu" else 16
+            peak = sms * lanes * peaks["sm_max_mhz"] * 1e6 / 1e12
+            ach = alg["inst"] / (ms * 1e-3) / 1e12
+            unit = "T FP32-inst/s" if alg["bound"] == "alu" else "T rsqrt/s"
+            d["roofline"] = dict(bound=alg["bound"], achieved=ach, peak=peak, unit=unit, frac=ach / peak)
+            d["fp32_tflops"] = alg["flops"] / (ms * 1e-3) / 1e12
             if "bytes" in alg:
                 gbs = alg["bytes"] / (ms * 1e-3) / 1e9
                 d["hbm"] = dict(achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=gbs / peaks["hbm_gbs"])
@@ -630,8 +677,9 @@ def run_ours(args):
     rf = dict(kern[dominant]["roofline"])
     rf["kernel"] = dominant
     rf["traffic"] = None
-    rf["peak_source"] = peaks["src"] if rf["bound"] != "alu" else \
-        "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (sms, peaks["sm_max_mhz"])
+    rf["peak_source"] = peaks["src"] if rf["bound"] not in ("alu", "mufu") else \
+        "derived: %d SMs x %d lanes x %.0f MHz (max SM clock); FP32 pipe measured 127 FMA/clk/SM" % (
+            sms, 128 if rf["bound"] == "alu" else 16, peaks["sm_max_mhz"])
     out = {
         "metric": METRIC, "value": value, "unit": "work-items/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -722,6 +770,7 @@ def main():
     ap.add_argument("--only", default="")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="reduced sizes for profiler captures")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch comparison")
     args = ap.parse_args()
     global SMALL
     SMALL = args.small

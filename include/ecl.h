@@ -103,6 +103,18 @@ typedef struct ecl_worker_stat {
     uint32_t chunks;     /* chunks it computed */
 } ecl_worker_stat;
 
+/* One batch of "binomial_batch" (80 bytes, the layout of the device table). */
+typedef struct ecl_binomial_instance {
+    const float *S, *K, *T, *sigma; /* device arrays of n values */
+    const int32_t *steps;           /* device int32[n], 1..2048 */
+    float *price;                   /* device float[n] */
+    float *greeks;                  /* device float2[n] (delta, vega) or NULL */
+    int64_t first;                  /* first option of this batch in the NDRange */
+    int64_t n;                      /* options in this batch */
+    float r;                        /* risk-free rate */
+    int32_t pad;
+} ecl_binomial_instance;
+
 /* ---------------------------------------------------------------- engine */
 
 /* Creates an engine on CUDA device `device_ordinal`.  `cuda_stream` is a
@@ -324,6 +336,15 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   backward induction in FP32 by one warp per option; with greeks the
  *   exact derivatives of the lattice price with respect to S and sigma
  *   (forward mode through the same lattice).
+ *
+ * "binomial_batch"  (4 args, out pattern 1:32, lws 32)  many option batches
+ *   of uneven size in one NDRange and one persistent launch:
+ *     0 B instances ecl_binomial_instance[count] (device, 16-byte aligned)
+ *     1 S int32 count  2 S int64 total options  3 S int32 with_greeks
+ *   instance i prices options [first_i, first_i + n_i) of the NDRange (first
+ *   ascending from 0, sum of n_i = total) from its own arrays; with_greeks = 0
+ *   skips the delta/vega lattices for the whole batch.  The engine does not
+ *   see the arrays the table points to: the caller guarantees them.
  *
  * "gemm_bf16"  (6 args; lws 32768 = one 128 x 256 output tile; the
  *   scheduling unit is one row of tiles)

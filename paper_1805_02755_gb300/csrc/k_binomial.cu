@@ -160,7 +160,7 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     if (N < 1 || N > kMaxSteps) {  // outside the supported depths: NaN results
         if (lane == 0) {
             p.price[o] = __int_as_float(0x7fc00000);
-            if (G) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+            if (G && p.greeks) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
         }
         return;
     }
@@ -228,7 +228,7 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
             delta += 1.0f;
         }
         p.price[o] = price;
-        if (G) p.greeks[o] = make_float2(delta, V[0] * scale);
+        if (G && p.greeks) p.greeks[o] = make_float2(delta, V[0] * scale);
     }
 }
 
@@ -252,6 +252,74 @@ __global__ void __launch_bounds__(kWarp) k_binomial(BinoParams prm, SchedArgs s)
 {
     __shared__ float sh[(G ? 3 : 1) * kShNodes];
     BinoBody<G> b;
+    b.p = prm;
+    b.sh = sh;
+    drive(s, b);
+}
+
+// ---------------------------------------------------------------- batches
+// Many option batches of uneven size as one NDRange: instance i owns global
+// options [first_i, first_i + n_i); a work-group (option) finds its instance
+// by binary search over `first` (ascending, first_0 = 0).  Mirrors
+// ecl_binomial_instance in include/ecl.h.
+struct BinoInstance {
+    const float *S, *K, *T, *sigma;
+    const int *steps;
+    float *price;
+    float2 *greeks;  // may be NULL
+    int64_t first;
+    int64_t n;
+    float r;
+    int32_t pad;
+};
+static_assert(sizeof(BinoInstance) == 80, "ecl_binomial_instance layout");
+
+struct BinoBatchParams {
+    const BinoInstance *inst;
+    int32_t count;
+    int64_t total;
+};
+
+template <bool G>
+struct BinoBatchBody {
+    using Params = BinoBatchParams;
+    Params p;
+    float *sh;
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const int64_t o = (int64_t)(off + t);
+        if (o >= p.total) return;
+        int lo = 0, hi = p.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&p.inst[mid].first) <= o) lo = mid;
+            else hi = mid - 1;
+        }
+        const BinoInstance &in = p.inst[lo];
+        const int64_t local = o - in.first;
+        if (local < 0 || local >= in.n) return;
+        BinoParams bp;
+        bp.S = in.S;
+        bp.K = in.K;
+        bp.T = in.T;
+        bp.sigma = in.sigma;
+        bp.steps = in.steps;
+        bp.r = in.r;
+        bp.n = in.n;
+        bp.price = in.price;
+        bp.greeks = G ? in.greeks : nullptr;
+        price_option<G>(bp, local, sh);
+    }
+};
+
+template <bool G>
+__global__ void __launch_bounds__(kWarp) k_binomial_batch(BinoBatchParams prm, SchedArgs s)
+{
+    __shared__ float sh[(G ? 3 : 1) * kShNodes];
+    BinoBatchBody<G> b;
     b.p = prm;
     b.sh = sh;
     drive(s, b);
@@ -328,7 +396,56 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     return ECL_OK;
 }
 
+// ---- binomial_batch: table of instances, count, total options, with_greeks
+ecl_status v_batch(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    const int64_t count = a.i32(1), total = a.i64(2);
+    if (count <= 0 || total <= 0) {
+        err = "count and total must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (a.bytes[0] < (uint64_t)count * sizeof(BinoInstance) || (uintptr_t)a.ptr[0] % 16) {
+        err = "the instance table must hold count 16-byte aligned entries of 80 bytes";
+        return ECL_ERR_BUFFER;
+    }
+    if (lws != kWarp) {
+        err = "lws must be 32 (one warp prices one option)";
+        return ECL_ERR_SIZE;
+    }
+    if (gws < (uint64_t)total * kWarp) {
+        err = "the NDRange (32 work-items per option) does not cover the options";
+        return ECL_ERR_SIZE;
+    }
+    return ECL_OK;
+}
+
+int batch_ctas_per_sm() { return occ((const void *)k_binomial_batch<true>); }
+
+ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    BinoBatchParams p;
+    p.inst = a.buf<const BinoInstance>(0);
+    p.count = a.i32(1);
+    p.total = a.i64(2);
+    if (a.i32(3))
+        k_binomial_batch<true><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    else
+        k_binomial_batch<false><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
+}
+
 }  // namespace
+
+extern const KernelDesc kBinomialBatch = {
+    "binomial_batch", 4,
+    {{"instances", A_BUF_IN}, {"count", A_I32}, {"total", A_I64}, {"with_greeks", A_I32}},
+    1, 0, kWarp, 0, v_batch, grain, nchunks, batch_ctas_per_sm, l_batch,
+};
 
 extern const KernelDesc kBinomial = {
     "binomial", 9,

@@ -14,6 +14,7 @@ extern const KernelDesc kNBodyAdjoint;
 extern const KernelDesc kNBodyEnergy;
 extern const KernelDesc kNBodyFD;
 extern const KernelDesc kBinomial;
+extern const KernelDesc kBinomialBatch;
 extern const KernelDesc kGemmBF16;
 extern const KernelDesc kGemmSplit3;
 extern const KernelDesc kCastBF16;
@@ -27,6 +28,7 @@ static const KernelDesc *const kAll[] = {
     &kNBodyEnergy,
     &kNBodyFD,
     &kBinomial,
+    &kBinomialBatch,
     &kGemmBF16,
     &kGemmSplit3,
     &kCastBF16,
