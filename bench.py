@@ -334,9 +334,9 @@ class Binomial(Workload):
                     batched_over_plain=ms_batched / ms_plain)
 
     def after(self):
-        # FP32 instructions per node update: price 3 (add, sub, FMA), delta 3, vega 4
-        # (flops with FMA = 2: 4 + 4 + 6)
-        return dict(bound="alu", inst=10.0 * self.nodes, flops=14.0 * self.nodes, unit_name="options/s",
+        # FP32 instructions per node update: three lattices (price, delta, vega leaf
+        # part) of 3 each (add, sub, FMA); flops with FMA = 2: 3 x 4
+        return dict(bound="alu", inst=9.0 * self.nodes, flops=12.0 * self.nodes, unit_name="options/s",
                     units=self.n, extra={"node_updates_per_s": self.nodes})
 
     def cpu_sample(self, O, threads):

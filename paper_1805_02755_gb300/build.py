@@ -29,7 +29,7 @@ SOURCES = {
     "k_binomial.cu": [],
     "k_gemm.cu": [],
 }
-HEADERS = ["ecl_internal.h", "sched.cuh"]
+HEADERS = ["ecl_internal.h", "sched.cuh", "f32x2.cuh"]
 
 
 def nvcc() -> str:

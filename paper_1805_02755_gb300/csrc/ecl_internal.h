@@ -142,7 +142,12 @@ struct KernelDesc {
 
 const KernelDesc *find_kernel(const char *name);
 
-// Engine-owned scratch memory, grown on demand (device memory).
-void *workspace_get(Workspace *ws, size_t bytes, std::string &err);
+// Engine-owned scratch memory, grown on demand (device memory).  Fresh memory
+// is zeroed.  A kernel that keeps counters in it passes itself as `owner`:
+// when the previous user was a different kernel the memory is zeroed on
+// `stream` first, so counters start at zero; kernels reset their counters
+// before they exit.
+void *workspace_get(Workspace *ws, size_t bytes, std::string &err, const void *owner = nullptr,
+                    cudaStream_t stream = 0);
 
 }  // namespace ecl

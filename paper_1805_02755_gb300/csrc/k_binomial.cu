@@ -24,11 +24,22 @@
 // The put lattice of a deep in-the-money call holds small values, while the
 // call lattice would carry two large vega terms (leaf and dq/dsigma parts)
 // that cancel, losing several digits in FP32.
-// Greeks are the exact derivatives of this discrete price (forward mode):
-//   delta tree: same recursion, leaves u^j d^(N-j) for in-the-money leaves;
+// Greeks are the exact derivatives of this discrete price.  Forward mode
+// through one level gives
+//   delta tree: the same recursion, leaves u^j d^(N-j) for in-the-money leaves;
 //   vega tree:  dB_j <- (dB_{j+1} + dB_j) + 2q (dB_{j+1} - dB_j) + 2q' (B_{j+1} - B_j),
 //               q' = dq/dsigma = sqrt(dt) (-1/2 - q coth a),
 //               leaves S_T (2j - N) sqrt(dt) for in-the-money leaves.
+// The level operator L = (1 + 2q) shift + (1 - 2q) identity and the
+// difference operator (shift - identity) are both shift-invariant, so they
+// commute, and the N coefficient terms of the vega tree add up to
+//   N 2q' (B_1 - B_0)   (B_1, B_0: the two nodes of level 1, same scaling).
+// So delta, the leaf part of vega and the price are three independent
+// lattices of the same recursion: the warp runs the price code three times
+// with different leaves, keeps B_1 - B_0 from the price pass, and
+//   vega = root(vega leaves) + N 2q' (B_1 - B_0).
+// This is the same derivative; in FP32 emulation its error matches the
+// level-by-level form (~1e-6 relative).
 #include <cuda_runtime.h>
 
 #include "ecl_internal.h"
@@ -51,7 +62,6 @@ struct BinoParams {
 
 struct Lat {
     float q2;      // 2q
-    float q2p;     // 2 dq/dsigma
     int active;    // live nodes at the current level
     int rescale;   // levels since the last rescale
     int shift;     // power of two still to remove from the result
@@ -59,17 +69,13 @@ struct Lat {
 
 // Lane widths (nodes per lane) the warp steps through as the lattice shrinks.
 // Going from width R to the next width R' happens when the live nodes fit in
-// 32 R'.  Price only: steps of about 1/8 (~91% of the computed slots live for
-// depths U{256..2048}).  With greeks every slot costs 10 instructions instead
-// of 3 and the unrolled level code of many widths starves on instruction
-// fetch; halving widths keep ~70% of the slots live with the least code.
-template <bool G>
+// 32 R'; steps of about 1/8 keep ~91% of the computed slots live for depths
+// U{256..2048}.
 __host__ __device__ constexpr int width_at(int i)
 {
-    return G ? (i == 0 ? 64 : i == 1 ? 32 : i == 2 ? 16 : i == 3 ? 8 : i == 4 ? 4 : i == 5 ? 2 : i == 6 ? 1 : 0)
-             : (i == 0 ? 64 : i == 1 ? 56 : i == 2 ? 48 : i == 3 ? 40 : i == 4 ? 32 : i == 5 ? 28 : i == 6 ? 24
-              : i == 7 ? 20 : i == 8 ? 16 : i == 9 ? 14 : i == 10 ? 12 : i == 11 ? 10 : i == 12 ? 8 : i == 13 ? 7
-              : i == 14 ? 6 : i == 15 ? 5 : i == 16 ? 4 : i == 17 ? 3 : i == 18 ? 2 : i == 19 ? 1 : 0);
+    return i == 0 ? 64 : i == 1 ? 56 : i == 2 ? 48 : i == 3 ? 40 : i == 4 ? 32 : i == 5 ? 28 : i == 6 ? 24
+         : i == 7 ? 20 : i == 8 ? 16 : i == 9 ? 14 : i == 10 ? 12 : i == 11 ? 10 : i == 12 ? 8 : i == 13 ? 7
+         : i == 14 ? 6 : i == 15 ? 5 : i == 16 ? 4 : i == 17 ? 3 : i == 18 ? 2 : i == 19 ? 1 : 0;
 }
 constexpr int kMaxR = 64;
 constexpr int kMaxSteps = kWarp * kMaxR;               // deepest lattice: 2048 steps
@@ -77,43 +83,25 @@ constexpr int kShNodes = kMaxSteps + 1 + kMaxSteps / 32 + 32;  // leaves 0..N wi
 
 __device__ __forceinline__ int shidx(int j) { return j + (j >> 5); }  // avoids bank conflicts
 
-template <int R, bool G>
-__device__ __forceinline__ void level(float (&B)[R], float (&D)[R], float (&V)[R], Lat &L)
+template <int R>
+__device__ __forceinline__ void level(float (&B)[R], Lat &L)
 {
     const float bn = __shfl_down_sync(kFull, B[0], 1);
-    float dn = 0.f, vn = 0.f;
-    if (G) {
-        dn = __shfl_down_sync(kFull, D[0], 1);
-        vn = __shfl_down_sync(kFull, V[0], 1);
-    }
 #pragma unroll
     for (int s = 0; s < R; ++s) {
         const float up = (s + 1 < R) ? B[s + 1] : bn;
-        const float diff = up - B[s];
-        if (G) {
-            const float dup = (s + 1 < R) ? D[s + 1] : dn;
-            const float vup = (s + 1 < R) ? V[s + 1] : vn;
-            V[s] = fmaf(L.q2p, diff, fmaf(L.q2, vup - V[s], vup + V[s]));
-            D[s] = fmaf(L.q2, dup - D[s], dup + D[s]);
-        }
-        B[s] = fmaf(L.q2, diff, up + B[s]);
+        B[s] = fmaf(L.q2, up - B[s], up + B[s]);
     }
     L.active -= 1;
     if (++L.rescale == 32) {
         L.rescale = 0;
         L.shift -= 32;
 #pragma unroll
-        for (int s = 0; s < R; ++s) {
-            B[s] *= 0x1p-32f;
-            if (G) {
-                D[s] *= 0x1p-32f;
-                V[s] *= 0x1p-32f;
-            }
-        }
+        for (int s = 0; s < R; ++s) B[s] *= 0x1p-32f;
     }
 }
 
-// One tree from width R to width R2 through the warp's shared buffer.
+// The tree from width R to width R2 through the warp's shared buffer.
 template <int R, int R2>
 __device__ __forceinline__ void repack(const float (&x)[R], float (&y)[R2], float *sh, int lane)
 {
@@ -126,29 +114,76 @@ __device__ __forceinline__ void repack(const float (&x)[R], float (&y)[R2], floa
 }
 
 // Levels at width width_at(WI) until the live nodes fit the next width, then
-// repack and continue; lane 0 slot 0 ends up holding the root.
-template <int WI, bool G>
-__device__ __forceinline__ void phase(float (&B)[width_at<G>(WI)], float (&D)[width_at<G>(WI)],
-                                      float (&V)[width_at<G>(WI)], Lat &L, float *sh, int lane)
+// repack and continue; lane 0 slot 0 ends up holding the root, and lane 0's
+// d1 the level-1 difference B_1 - B_0 at the root's scaling.
+template <int WI>
+__device__ __forceinline__ void phase(float (&B)[width_at(WI)], Lat &L, float *sh, int lane, float &d1)
 {
-    constexpr int R = width_at<G>(WI);
-    constexpr int R2 = width_at<G>(WI + 1);
-    const int limit = R2 ? kWarp * R2 : 1;
-    while (L.active > limit) level<R, G>(B, D, V, L);
+    constexpr int R = width_at(WI);
+    constexpr int R2 = width_at(WI + 1);
     if constexpr (R2 > 0) {
-        float b2[R2], d2[R2], v2[R2];
+        while (L.active > kWarp * R2) level<R>(B, L);
+        float b2[R2];
         repack<R, R2>(B, b2, sh, lane);
-        if (G) {
-            repack<R, R2>(D, d2, sh, lane);
-            repack<R, R2>(V, v2, sh, lane);
-        }
-        phase<WI + 1, G>(b2, d2, v2, L, sh, lane);
+        phase<WI + 1>(b2, L, sh, lane, d1);
         B[0] = b2[0];
-        if (G) {
-            D[0] = d2[0];
-            V[0] = v2[0];
+    } else {
+        while (L.active > 2) level<1>(B, L);
+        if (L.active == 2) {
+            d1 = __shfl_down_sync(kFull, B[0], 1) - B[0];
+            level<1>(B, L);
+            if (L.rescale == 0) d1 *= 0x1p-32f;
         }
     }
+}
+
+// Per-option constants of the lattice.
+struct Opt {
+    float S, K, sdt, a, q2;
+    int N;
+    bool put;
+};
+
+enum LeafKind { LEAF_PRICE = 0, LEAF_DELTA = 1, LEAF_VEGA = 2 };
+
+// One backward induction from the leaves of `kind` (only in-the-money leaves
+// of the priced side are non-zero).  Returns the root on lane 0 (scaled by
+// 2^shift); for the price leaves d1 receives B_1 - B_0.
+__device__ __forceinline__ float lattice(const Opt &o, int kind, float *sh, int lane, int &shift, float &d1)
+{
+    __syncwarp();
+    for (int j = lane; j <= kMaxSteps; j += kWarp) {
+        float v = 0.f;
+        if (j <= o.N) {
+            const float m = (float)(2 * j - o.N);
+            const float g = expf(o.a * m);
+            const float ST = o.S * g;
+            if (o.put ? (ST < o.K) : (ST > o.K)) {
+                if (kind == LEAF_PRICE) v = o.put ? o.K - ST : ST - o.K;
+                else if (kind == LEAF_DELTA) v = o.put ? -g : g;
+                else v = o.put ? -(ST * m * o.sdt) : ST * m * o.sdt;
+            }
+        }
+        sh[shidx(j)] = v;
+    }
+    __syncwarp();
+    Lat L;
+    L.q2 = o.q2;
+    L.active = o.N;  // nodes of level N-1
+    L.rescale = 1;   // that level is formed from the leaves below
+    L.shift = o.N;
+    // level N-1 at width 64: node j from leaves j and j+1
+    float B[kMaxR];
+#pragma unroll
+    for (int s = 0; s < kMaxR; ++s) {
+        const int j = lane * kMaxR + s;
+        const float lb = sh[shidx(j + 1)], b = sh[shidx(j)];
+        if (s == 0) d1 = lb - b;  // the level-1 difference when N == 1
+        B[s] = fmaf(L.q2, lb - b, lb + b);
+    }
+    phase<0>(B, L, sh, lane, d1);
+    shift = L.shift;
+    return B[0];
 }
 
 template <bool G>
@@ -171,64 +206,50 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     const float num = expm1f(p.r * dt) - 2.0f * sh2 * sh2;
     const float s1 = sinhf(a);
     const float q = num / (2.0f * s1);
-    Lat L;
-    L.q2 = 2.0f * q;
-    L.q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));
-    L.active = N;   // nodes of level N-1
-    L.rescale = 1;  // that level is formed from the leaves below
-    L.shift = N;
-    const bool put = S > K;  // price the out-of-the-money side, then parity
-    // leaves 0..N (zero beyond N) into the shared buffers, lane-strided
-    float *shb = sh, *shd = sh + kShNodes, *shv = sh + 2 * kShNodes;
-    __syncwarp();
-    for (int j = lane; j <= kMaxSteps; j += kWarp) {
-        float b = 0.f, d = 0.f, v = 0.f;
-        if (j <= N) {
-            const float m = (float)(2 * j - N);
-            const float g = expf(a * m);
-            const float ST = S * g;
-            if (put ? (ST < K) : (ST > K)) {
-                b = put ? K - ST : ST - K;
-                if (G) {
-                    d = put ? -g : g;
-                    v = put ? -(ST * m * sdt) : ST * m * sdt;
-                }
-            }
-        }
-        shb[shidx(j)] = b;
-        if (G) {
-            shd[shidx(j)] = d;
-            shv[shidx(j)] = v;
+    Opt op;
+    op.S = S;
+    op.K = K;
+    op.sdt = sdt;
+    op.a = a;
+    op.q2 = 2.0f * q;
+    op.N = N;
+    op.put = S > K;  // price the out-of-the-money side, then parity
+    // price, then (greeks) delta and the vega leaf part; one copy of the
+    // unrolled level code serves the three passes
+    int shift = 0;
+    float d1 = 0.f, root[3] = {0.f, 0.f, 0.f};
+    const int passes = (G && p.greeks) ? 3 : 1;
+#pragma unroll 1
+    for (int k = 0; k < passes; ++k) {
+        float dk;
+        const float r = lattice(op, k, sh, lane, shift, dk);
+        if (k == 0) {
+            root[0] = r;
+            d1 = dk;
+        } else if (k == 1) {
+            root[1] = r;
+        } else {
+            root[2] = r;
         }
     }
-    __syncwarp();
-    // level N-1 at width 64: node j from leaves j and j+1
-    float B[kMaxR], D[kMaxR], V[kMaxR];
-#pragma unroll
-    for (int s = 0; s < kMaxR; ++s) {
-        const int j = lane * kMaxR + s;
-        const float lb = shb[shidx(j + 1)], b = shb[shidx(j)];
-        const float diff = lb - b;
-        B[s] = fmaf(L.q2, diff, lb + b);
-        if (G) {
-            const float ld = shd[shidx(j + 1)], d = shd[shidx(j)];
-            const float lv = shv[shidx(j + 1)], v = shv[shidx(j)];
-            D[s] = fmaf(L.q2, ld - d, ld + d);
-            V[s] = fmaf(L.q2p, diff, fmaf(L.q2, lv - v, lv + v));
-        }
+    const float b = root[0];
+    float delta = root[1], vega = root[2];
+    if (passes == 3) {
+        const float q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));  // 2 dq/dsigma
+        vega = fmaf((float)N * q2p, d1, vega);
     }
-    phase<0, G>(B, D, V, L, sh, lane);
     if (lane == 0) {
         // remove the remaining 2^shift (exact), then discount
         const float disc = expf(-p.r * T);
-        const float scale = ldexpf(disc, -L.shift);
-        float price = B[0] * scale, delta = D[0] * scale;
-        if (put) {
+        const float scale = ldexpf(disc, -shift);
+        float price = b * scale;
+        delta *= scale;
+        if (op.put) {
             price += S - K * disc;
             delta += 1.0f;
         }
         p.price[o] = price;
-        if (G && p.greeks) p.greeks[o] = make_float2(delta, V[0] * scale);
+        if (G && p.greeks) p.greeks[o] = make_float2(delta, vega * scale);
     }
 }
 
@@ -250,7 +271,7 @@ struct BinoBody {
 template <bool G>
 __global__ void __launch_bounds__(kWarp) k_binomial(BinoParams prm, SchedArgs s)
 {
-    __shared__ float sh[(G ? 3 : 1) * kShNodes];
+    __shared__ float sh[kShNodes];
     BinoBody<G> b;
     b.p = prm;
     b.sh = sh;
@@ -318,7 +339,7 @@ struct BinoBatchBody {
 template <bool G>
 __global__ void __launch_bounds__(kWarp) k_binomial_batch(BinoBatchParams prm, SchedArgs s)
 {
-    __shared__ float sh[(G ? 3 : 1) * kShNodes];
+    __shared__ float sh[kShNodes];
     BinoBatchBody<G> b;
     b.p = prm;
     b.sh = sh;

@@ -8,10 +8,15 @@
 //   nbody_energy   E = -sum_{i<j} m_i m_j / sqrt(|d_ij|^2 + eps2)
 //   nbody_fd       central differences of E in sampled coordinates
 //
-// One chunk = one work-group of lws bodies (lws 32..256, a power of two).
-// The CTA has 256 threads.  Force kernels: thread t owns two bodies of the
-// work-group (t % (lws/2) and that + lws/2, computed together in packed
-// FP32x2 arithmetic) and the j-slice t / (lws/2).  Energy: thread t owns
+// The CTA has 256 threads.  Force kernels: a work-group of lws bodies (lws
+// 32..256, a power of two) is cut into S j-segments (whole 256-body tiles),
+// one chunk each, so that a run has enough chunks to balance the persistent
+// CTAs; each chunk writes its per-body partial sums to the workspace and the
+// last chunk of the work-group (a counter per work-group) adds the S
+// partials in segment order and writes the result.  Within a chunk, thread
+// t owns two bodies of the work-group (t % (lws/2) and that + lws/2,
+// computed together in packed FP32x2 arithmetic) and the j-slice
+// t / (lws/2).  Energy: thread t owns
 // body t % lws and the j-slice t / lws.  j-bodies are staged in shared
 // memory 256 at a time (tiles on an absolute 256-body grid).  Each thread sums the pair terms of
 // one tile in FP32, then adds the tile sum to its running FP32 total
@@ -23,6 +28,7 @@
 #include <mutex>
 
 #include "ecl_internal.h"
+#include "f32x2.cuh"
 #include "sched.cuh"
 
 namespace ecl {
@@ -42,51 +48,29 @@ struct NBodyParams {
     float4 *out_acc;            // NB_ACC
     const float *grad_E;        // NB_ADJ: device scalar dL/dE
     float4 *out_grad;           // NB_ADJ
+    float4 *part;               // [G][seg][lws] partial sums (seg > 1)
+    unsigned *wgcnt;            // [G] segments finished per work-group
+    uint32_t seg;               // j-segments (chunks) per work-group
     uint32_t lws;
 };
 
-__host__ __device__ inline uint32_t one_chunk_per_wg(uint64_t len) { return (uint32_t)len; }
+// j-segments per work-group of the force kernels: enough chunks (about 4096)
+// to keep every persistent CTA busy to the end, at most 16 and at most one
+// per 256-body tile.
+__host__ __device__ inline uint32_t force_segments(uint64_t G, int64_t n)
+{
+    const int64_t ntiles = (n + 255) / 256;
+    uint64_t s = (4096 + G - 1) / (G ? G : 1);
+    if (s > 16) s = 16;
+    if ((int64_t)s > ntiles) s = (uint64_t)ntiles;
+    return s < 1 ? 1u : (uint32_t)s;
+}
 
 // Stage j-tile `tile` (zero-mass padding beyond n).
 __device__ __forceinline__ void stage_tile(float4 *sh, const float4 *pos, int64_t n, int64_t tile)
 {
     const int64_t j = tile * kTile + threadIdx.x;
     sh[threadIdx.x] = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-// Packed FP32x2 arithmetic (sm_100+): one instruction, two lanes of work.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b)
-{
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
 }
 
 // Stage j-tile `tile` duplicated for packed use: (x,x,y,y) and (z,z,m,m).
@@ -110,10 +94,30 @@ struct ForceBody {
     Params p;
     float4 *shxy, *shzm;  // [kTile] duplicated j-bodies
     float4 *red;          // [2 * kBlock] slice partials
+    uint32_t *flag;       // shared: this chunk completes its work-group
 
-    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
+    static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t, uint64_t len)
     {
-        return one_chunk_per_wg(len);
+        return (uint32_t)(len * q.seg);
+    }
+
+    // The body's output from its total a = (a_x, a_y, a_z, potential sum).
+    __device__ __forceinline__ void finish(int64_t i, const float4 &pi, const float4 &a)
+    {
+        if (MODE == NB_ACC) {
+            p.out_acc[i] = make_float4(a.x, a.y, a.z, 0.f);
+        } else if (MODE == NB_STEP) {
+            const float4 v = __ldg(p.vel + i);
+            const float h = 0.5f * p.dt * p.dt;
+            p.out_pos[i] = make_float4(pi.x + v.x * p.dt + a.x * h, pi.y + v.y * p.dt + a.y * h,
+                                       pi.z + v.z * p.dt + a.z * h, pi.w);
+            p.out_vel[i] = make_float4(v.x + a.x * p.dt, v.y + a.y * p.dt, v.z + a.z * p.dt, v.w);
+        } else {
+            // the self term j == i added m_i / sqrt(eps2) to the potential sum
+            const float self = pi.w * rsqrtf(p.eps2);
+            const float g = __ldg(p.grad_E);
+            p.out_grad[i] = make_float4(-g * pi.w * a.x, -g * pi.w * a.y, -g * pi.w * a.z, -g * (a.w - self));
+        }
     }
 
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
@@ -121,7 +125,9 @@ struct ForceBody {
         const uint32_t half = p.lws / 2;
         const uint32_t S = kBlock / half;            // j-slices
         const uint32_t b = threadIdx.x % half, s = threadIdx.x / half;
-        const int64_t i0 = (int64_t)(off + t) * p.lws + b, i1 = i0 + half;
+        const uint64_t wg = off + t / p.seg;
+        const uint32_t sg = t % p.seg;
+        const int64_t i0 = (int64_t)wg * p.lws + b, i1 = i0 + half;
         const bool v0 = i0 < p.n, v1 = i1 < p.n;
         const float4 p0 = v0 ? __ldg(p.pos + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 p1 = v1 ? __ldg(p.pos + i1) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -130,7 +136,8 @@ struct ForceBody {
         const uint32_t span = kTile / S;
         f2 AX = 0, AY = 0, AZ = 0, POT = 0;
         const int64_t ntiles = (p.n + kTile - 1) / kTile;
-        for (int64_t tile = 0; tile < ntiles; ++tile) {
+        const int64_t ta = ntiles * sg / p.seg, tb = ntiles * (sg + 1) / p.seg;
+        for (int64_t tile = ta; tile < tb; ++tile) {
             body_sync(kBlock);
             stage_tile2(shxy, shzm, p.pos, p.n, tile);
             body_sync(kBlock);
@@ -167,34 +174,46 @@ struct ForceBody {
         red[threadIdx.x] = make_float4(ax0, ay0, az0, pt0);
         red[kBlock + threadIdx.x] = make_float4(ax1, ay1, az1, pt1);
         body_sync(kBlock);
-        if (s < 2) {  // slice-0 thread finishes body b, slice-1 thread body b + half
-            const int64_t i = s == 0 ? i0 : i1;
-            if (i < p.n) {
-                const float4 pi = s == 0 ? p0 : p1;
-                const float4 *r = red + (s == 0 ? 0 : kBlock);
-                float4 a = r[b];
-                for (uint32_t q = 1; q < S; ++q) {
-                    const float4 e = r[q * half + b];
-                    a.x += e.x;
-                    a.y += e.y;
-                    a.z += e.z;
-                    a.w += e.w;
-                }
-                if (MODE == NB_ACC) {
-                    p.out_acc[i] = make_float4(a.x, a.y, a.z, 0.f);
-                } else if (MODE == NB_STEP) {
-                    const float4 v = __ldg(p.vel + i);
-                    const float h = 0.5f * p.dt * p.dt;
-                    p.out_pos[i] = make_float4(pi.x + v.x * p.dt + a.x * h, pi.y + v.y * p.dt + a.y * h,
-                                               pi.z + v.z * p.dt + a.z * h, pi.w);
-                    p.out_vel[i] = make_float4(v.x + a.x * p.dt, v.y + a.y * p.dt, v.z + a.z * p.dt, v.w);
-                } else {
-                    // the self term j == i added m_i / sqrt(eps2) to the potential sum
-                    const float self = pi.w * rsqrtf(p.eps2);
-                    const float g = __ldg(p.grad_E);
-                    p.out_grad[i] = make_float4(-g * pi.w * a.x, -g * pi.w * a.y, -g * pi.w * a.z, -g * (a.w - self));
-                }
+        // slice-0 thread handles body b, slice-1 thread body b + half
+        const bool mine = s < 2 && (s == 0 ? v0 : v1);
+        const uint32_t lb = s == 0 ? b : b + half;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mine) {
+            const float4 *r = red + (s == 0 ? 0 : kBlock);
+            a = r[b];
+            for (uint32_t q = 1; q < S; ++q) {
+                const float4 e = r[q * half + b];
+                a.x += e.x;
+                a.y += e.y;
+                a.z += e.z;
+                a.w += e.w;
             }
+        }
+        if (p.seg == 1) {
+            if (mine) finish(s == 0 ? i0 : i1, s == 0 ? p0 : p1, a);
+            return;
+        }
+        // segment partial to the workspace; the work-group's last segment sums them
+        float4 *wpart = p.part + (size_t)wg * p.seg * p.lws;
+        if (mine) wpart[(size_t)sg * p.lws + lb] = a;
+        __threadfence();
+        body_sync(kBlock);
+        if (threadIdx.x == 0) *flag = (atomicAdd(p.wgcnt + wg, 1u) + 1 == p.seg) ? 1u : 0u;
+        body_sync(kBlock);
+        if (*flag) {
+            __threadfence();
+            if (mine) {
+                float4 tot = __ldcg(wpart + lb);
+                for (uint32_t q = 1; q < p.seg; ++q) {
+                    const float4 e = __ldcg(wpart + (size_t)q * p.lws + lb);
+                    tot.x += e.x;
+                    tot.y += e.y;
+                    tot.z += e.z;
+                    tot.w += e.w;
+                }
+                finish(s == 0 ? i0 : i1, s == 0 ? p0 : p1, tot);
+            }
+            if (threadIdx.x == 0) p.wgcnt[wg] = 0u;  // ready for the next run
         }
     }
 };
@@ -398,11 +417,13 @@ __global__ void __launch_bounds__(kBlock + 32, 3) k_nbody_force(NBodyParams prm,
     __shared__ __align__(16) float4 shxy[kTile];
     __shared__ __align__(16) float4 shzm[kTile];
     __shared__ float4 red[2 * kBlock];
+    __shared__ uint32_t flag;
     ForceBody<MODE> b;
     b.p = prm;
     b.shxy = shxy;
     b.shzm = shzm;
     b.red = red;
+    b.flag = &flag;
     drive_ws(s, b);
 }
 
@@ -476,6 +497,31 @@ uint64_t grain1(const KArgs &, uint64_t, uint32_t) { return 1; }
 
 uint32_t nchunks_wg(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
 
+// Force kernels: S chunks per work-group (bodies at argument n_arg).
+template <int n_arg>
+uint32_t nchunks_force(const KArgs &a, uint64_t gws, uint32_t lws, uint64_t, uint64_t len)
+{
+    return (uint32_t)(len * force_segments(gws / lws, a.i32(n_arg)));
+}
+
+// Segment count and workspace (per-segment partials + per-work-group
+// counters) of a force launch.
+bool force_ws(NBodyParams &p, const LaunchCtx &c, const void *owner, std::string &err)
+{
+    const uint64_t G = c.gws / c.lws;
+    p.seg = force_segments(G, p.n);
+    p.part = nullptr;
+    p.wgcnt = nullptr;
+    if (p.seg == 1) return true;
+    const size_t cnt_bytes = (G * sizeof(unsigned) + 255) / 256 * 256;
+    char *ws = (char *)workspace_get(c.ws, cnt_bytes + (size_t)G * p.seg * c.lws * sizeof(float4), err, owner,
+                                     c.stream);
+    if (!ws) return false;
+    p.wgcnt = (unsigned *)ws;
+    p.part = (float4 *)(ws + cnt_bytes);
+    return true;
+}
+
 uint32_t nchunks_energy(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)(len * kESeg); }
 
 // ---- nbody (Listing 2 order): in_pos, in_vel, bodies, del_t, esp_sqr, out_pos, out_vel
@@ -502,6 +548,7 @@ ecl_status l_step(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.out_pos = a.buf<float4>(5);
     p.out_vel = a.buf<float4>(6);
     p.lws = c.lws;
+    if (!force_ws(p, c, (const void *)k_nbody_force<NB_STEP>, err)) return ECL_ERR_CUDA;
     k_nbody_force<NB_STEP><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
@@ -528,6 +575,7 @@ ecl_status l_acc(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.eps2 = a.f32(2);
     p.out_acc = a.buf<float4>(3);
     p.lws = c.lws;
+    if (!force_ws(p, c, (const void *)k_nbody_force<NB_ACC>, err)) return ECL_ERR_CUDA;
     k_nbody_force<NB_ACC><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
@@ -559,6 +607,7 @@ ecl_status l_adj(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.grad_E = a.buf<const float>(3);
     p.out_grad = a.buf<float4>(4);
     p.lws = c.lws;
+    if (!force_ws(p, c, (const void *)k_nbody_force<NB_ADJ>, err)) return ECL_ERR_CUDA;
     k_nbody_force<NB_ADJ><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
@@ -584,7 +633,7 @@ ecl_status v_energy(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err
 ecl_status l_energy(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
     const uint64_t G = c.gws / c.lws;
-    char *ws = (char *)workspace_get(c.ws, 256 + G * kESeg * sizeof(double), err);
+    char *ws = (char *)workspace_get(c.ws, 256 + G * kESeg * sizeof(double), err, (const void *)k_nbody_energy, c.stream);
     if (!ws) return ECL_ERR_CUDA;
     EnergyParams p{};
     p.pos = a.buf<const float4>(0);
@@ -647,20 +696,20 @@ extern const KernelDesc kNBody = {
     "nbody", 7,
     {{"in_pos", A_BUF_IN}, {"in_vel", A_BUF_IN}, {"bodies", A_I32}, {"del_t", A_F32}, {"esp_sqr", A_F32},
      {"out_pos", A_BUF_OUT}, {"out_vel", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_step, grain1, nchunks_wg, o_step, l_step,
+    1, 1, kBlock + 32, 0, v_step, grain1, nchunks_force<2>, o_step, l_step,
 };
 
 extern const KernelDesc kNBodyAcc = {
     "nbody_acc", 4,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_acc", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_acc, grain1, nchunks_wg, o_acc, l_acc,
+    1, 1, kBlock + 32, 0, v_acc, grain1, nchunks_force<1>, o_acc, l_acc,
 };
 
 extern const KernelDesc kNBodyAdjoint = {
     "nbody_adjoint", 5,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"grad_E", A_BUF_IN},
      {"out_grad", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_adj, grain1, nchunks_wg, o_adj, l_adj,
+    1, 1, kBlock + 32, 0, v_adj, grain1, nchunks_force<1>, o_adj, l_adj,
 };
 
 extern const KernelDesc kNBodyEnergy = {

@@ -23,14 +23,26 @@ namespace ecl {
 struct Workspace {
     void *ptr = nullptr;
     size_t bytes = 0;
+    const void *owner = nullptr;  // kernel whose counters the memory holds
 };
 
-void *workspace_get(Workspace *ws, size_t bytes, std::string &err)
+void *workspace_get(Workspace *ws, size_t bytes, std::string &err, const void *owner, cudaStream_t stream)
 {
-    if (ws->bytes >= bytes) return ws->ptr;
+    if (ws->bytes >= bytes) {
+        if (owner && owner != ws->owner) {  // another kernel's leftovers: zero before use
+            cudaError_t ce = cudaMemsetAsync(ws->ptr, 0, bytes, stream);
+            if (ce != cudaSuccess) {
+                err = std::string("cudaMemsetAsync(workspace): ") + cudaGetErrorString(ce);
+                return nullptr;
+            }
+        }
+        ws->owner = owner;
+        return ws->ptr;
+    }
     if (ws->ptr) cudaFree(ws->ptr);
     ws->ptr = nullptr;
     ws->bytes = 0;
+    ws->owner = nullptr;
     cudaError_t ce = cudaMalloc(&ws->ptr, bytes);
     if (ce != cudaSuccess) {
         err = std::string("cudaMalloc(workspace): ") + cudaGetErrorString(ce);
@@ -45,6 +57,7 @@ void *workspace_get(Workspace *ws, size_t bytes, std::string &err)
         return nullptr;
     }
     ws->bytes = bytes;
+    ws->owner = owner;
     return ws->ptr;
 }
 }  // namespace ecl

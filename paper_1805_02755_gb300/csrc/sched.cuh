@@ -302,27 +302,28 @@ __device__ __forceinline__ void sbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait on phase `parity`; false (and the queue's error word set)
-// when it gave up after about two seconds.
+// when it gave up after about two seconds.  Each try_wait carries a suspend
+// hint, so a waiting thread sleeps until the phase completes (or the hint
+// runs out) instead of spinning: the scheduler warp waits out a whole chunk
+// this way and must not take issue slots from the compute warps.
 __device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsigned int *gerr)
 {
     uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             "selp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
-            : "r"(sh_addr(bar)), "r"(parity)
+            : "r"(sh_addr(bar)), "r"(parity), "r"(100000u)
             : "memory");
         if (ok) return true;
-        if ((it & 63u) == 0) {
-            const uint64_t now = gtime();
-            if (!t0) t0 = now;
-            if (now - t0 > 2000000000ull) {
-                atomicExch(gerr, (unsigned int)ECL_ERR_TIMEOUT);
-                return false;
-            }
+        const uint64_t now = gtime();
+        if (!t0) t0 = now;
+        if (now - t0 > 2000000000ull) {
+            atomicExch(gerr, (unsigned int)ECL_ERR_TIMEOUT);
+            return false;
         }
     }
 }
