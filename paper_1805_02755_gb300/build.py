@@ -3,7 +3,10 @@
 Each .cu file is compiled to an object in parallel, then the objects are
 linked into one shared library next to this file.  The Mandelbrot unit is
 compiled with -fmad=false (its counts must match a correctly rounded host
-evaluation bit for bit).
+evaluation bit for bit).  The NBody unit is compiled with -ftz=true: every
+FP32 value there is far from the subnormal range (r^2 >= eps^2 > 0), and
+without subnormal handling rsqrtf is the bare hardware reciprocal square
+root instead of a range check, a scaling and the root.
 """
 from __future__ import annotations
 
@@ -25,7 +28,7 @@ SOURCES = {
     "registry.cu": [],
     "k_mandelbrot.cu": ["-fmad=false"],
     "k_gaussian.cu": [],
-    "k_nbody.cu": [],
+    "k_nbody.cu": ["-ftz=true"],
     "k_binomial.cu": [],
     "k_gemm.cu": [],
 }

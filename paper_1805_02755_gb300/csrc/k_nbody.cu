@@ -34,8 +34,13 @@
 namespace ecl {
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 256;   // energy and finite-difference CTAs
 constexpr int kTile = 256;
+constexpr int kFBlock = 256;  // force CTA: 8 compute warps (+ the scheduler warp), 3 per SM
+constexpr int kFTile = 256;   // j-bodies per staged force tile
+// Force shared memory: two duplicated tiles (x,x,y,y) and (z,z,m,m), double
+// buffered; the slice partials reuse the first half after the tile loop.
+constexpr size_t kFSmem = 2 * 2 * kFTile * sizeof(float4);
 
 enum NMode : uint32_t { NB_STEP = 0, NB_ACC = 1, NB_ADJ = 2 };
 
@@ -54,13 +59,13 @@ struct NBodyParams {
     uint32_t lws;
 };
 
-// j-segments per work-group of the force kernels: enough chunks (about 4096)
-// to keep every persistent CTA busy to the end, at most 16 and at most one
-// per 256-body tile.
+// j-segments per work-group of the force kernels: enough chunks (about 8192,
+// ~18 per resident CTA) that the last chunks, which set the end of the run,
+// are short; at most 16 and at most one per staged tile.
 __host__ __device__ inline uint32_t force_segments(uint64_t G, int64_t n)
 {
-    const int64_t ntiles = (n + 255) / 256;
-    uint64_t s = (4096 + G - 1) / (G ? G : 1);
+    const int64_t ntiles = (n + kFTile - 1) / kFTile;
+    uint64_t s = (8192 + G - 1) / (G ? G : 1);
     if (s > 16) s = 16;
     if ((int64_t)s > ntiles) s = (uint64_t)ntiles;
     return s < 1 ? 1u : (uint32_t)s;
@@ -73,11 +78,16 @@ __device__ __forceinline__ void stage_tile(float4 *sh, const float4 *pos, int64_
     sh[threadIdx.x] = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Stage j-tile `tile` duplicated for packed use: (x,x,y,y) and (z,z,m,m).
-__device__ __forceinline__ void stage_tile2(float4 *shxy, float4 *shzm, const float4 *pos, int64_t n, int64_t tile)
+// j-body `tile * kFTile + threadIdx.x` (zero-mass padding beyond n).
+__device__ __forceinline__ float4 tile_body(const float4 *pos, int64_t n, int64_t tile)
 {
-    const int64_t j = tile * kTile + threadIdx.x;
-    const float4 q = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t j = tile * kFTile + threadIdx.x;
+    return (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Store one j-body duplicated for packed use: (x,x,y,y) and (z,z,m,m).
+__device__ __forceinline__ void put_dup(float4 *shxy, float4 *shzm, const float4 &q)
+{
     shxy[threadIdx.x] = make_float4(q.x, q.x, q.y, q.y);
     shzm[threadIdx.x] = make_float4(q.z, q.z, q.w, q.w);
 }
@@ -89,11 +99,11 @@ __device__ __forceinline__ void stage_tile2(float4 *shxy, float4 *shzm, const fl
 //   s = (m_j inv)(inv inv), a += s d.
 template <uint32_t MODE>
 struct ForceBody {
-    static constexpr uint32_t kThreads = kBlock;
+    static constexpr uint32_t kThreads = kFBlock;
     using Params = NBodyParams;
     Params p;
-    float4 *shxy, *shzm;  // [kTile] duplicated j-bodies
-    float4 *red;          // [2 * kBlock] slice partials
+    float4 *shxy, *shzm;  // [2][kFTile] duplicated j-bodies, double-buffered
+    float4 *red;          // [2 * kFBlock] slice partials (aliases shxy)
     uint32_t *flag;       // shared: this chunk completes its work-group
 
     static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t, uint64_t len)
@@ -123,7 +133,7 @@ struct ForceBody {
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
         const uint32_t half = p.lws / 2;
-        const uint32_t S = kBlock / half;            // j-slices
+        const uint32_t S = kFBlock / half;            // j-slices
         const uint32_t b = threadIdx.x % half, s = threadIdx.x / half;
         const uint64_t wg = off + t / p.seg;
         const uint32_t sg = t % p.seg;
@@ -133,17 +143,23 @@ struct ForceBody {
         const float4 p1 = v1 ? __ldg(p.pos + i1) : make_float4(0.f, 0.f, 0.f, 0.f);
         const f2 X = pk(p0.x, p1.x), Y = pk(p0.y, p1.y), Z = pk(p0.z, p1.z);
         const f2 EPS = pk(p.eps2, p.eps2);
-        const uint32_t span = kTile / S;
+        const uint32_t span = kFTile / S;
         f2 AX = 0, AY = 0, AZ = 0, POT = 0;
-        const int64_t ntiles = (p.n + kTile - 1) / kTile;
+        const int64_t ntiles = (p.n + kFTile - 1) / kFTile;
         const int64_t ta = ntiles * sg / p.seg, tb = ntiles * (sg + 1) / p.seg;
+        // tiles double-buffered: the next tile's loads are in flight while
+        // the current one is computed, one barrier per tile
+        body_sync(kFBlock);  // the previous chunk is done with both buffers
+        if (ta < tb) put_dup(shxy, shzm, tile_body(p.pos, p.n, ta));
+        body_sync(kFBlock);
         for (int64_t tile = ta; tile < tb; ++tile) {
-            body_sync(kBlock);
-            stage_tile2(shxy, shzm, p.pos, p.n, tile);
-            body_sync(kBlock);
+            const uint32_t cur = (uint32_t)(tile - ta) & 1u;
+            const bool more = tile + 1 < tb;
+            float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (more) nxt = tile_body(p.pos, p.n, tile + 1);
             f2 TX = 0, TY = 0, TZ = 0, TP = 0;
-            const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + s * span);
-            const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + s * span);
+            const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + cur * kFTile + s * span);
+            const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + cur * kFTile + s * span);
 #pragma unroll 8
             for (uint32_t k = 0; k < span; ++k) {
                 const ulonglong2 xy = qxy[k], zm = qzm[k];
@@ -163,6 +179,9 @@ struct ForceBody {
             AY = add2(AY, TY);
             AZ = add2(AZ, TZ);
             if (MODE == NB_ADJ) POT = add2(POT, TP);
+            // the other buffer was last read before the previous barrier
+            if (more) put_dup(shxy + (cur ^ 1u) * kFTile, shzm + (cur ^ 1u) * kFTile, nxt);
+            body_sync(kFBlock);
         }
         // combine the slices of each body in slice order
         float ax0, ax1, ay0, ay1, az0, az1, pt0, pt1;
@@ -170,16 +189,16 @@ struct ForceBody {
         upk(AY, ay0, ay1);
         upk(AZ, az0, az1);
         upk(POT, pt0, pt1);
-        body_sync(kBlock);
+        body_sync(kFBlock);
         red[threadIdx.x] = make_float4(ax0, ay0, az0, pt0);
-        red[kBlock + threadIdx.x] = make_float4(ax1, ay1, az1, pt1);
-        body_sync(kBlock);
+        red[kFBlock + threadIdx.x] = make_float4(ax1, ay1, az1, pt1);
+        body_sync(kFBlock);
         // slice-0 thread handles body b, slice-1 thread body b + half
         const bool mine = s < 2 && (s == 0 ? v0 : v1);
         const uint32_t lb = s == 0 ? b : b + half;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         if (mine) {
-            const float4 *r = red + (s == 0 ? 0 : kBlock);
+            const float4 *r = red + (s == 0 ? 0 : kFBlock);
             a = r[b];
             for (uint32_t q = 1; q < S; ++q) {
                 const float4 e = r[q * half + b];
@@ -197,9 +216,9 @@ struct ForceBody {
         float4 *wpart = p.part + (size_t)wg * p.seg * p.lws;
         if (mine) wpart[(size_t)sg * p.lws + lb] = a;
         __threadfence();
-        body_sync(kBlock);
+        body_sync(kFBlock);
         if (threadIdx.x == 0) *flag = (atomicAdd(p.wgcnt + wg, 1u) + 1 == p.seg) ? 1u : 0u;
-        body_sync(kBlock);
+        body_sync(kFBlock);
         if (*flag) {
             __threadfence();
             if (mine) {
@@ -412,17 +431,15 @@ struct FDBody {
 
 // ---------------------------------------------------------------- kernels
 template <uint32_t MODE>
-__global__ void __launch_bounds__(kBlock + 32, 3) k_nbody_force(NBodyParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kFBlock + 32, 3) k_nbody_force(NBodyParams prm, SchedArgs s)
 {
-    __shared__ __align__(16) float4 shxy[kTile];
-    __shared__ __align__(16) float4 shzm[kTile];
-    __shared__ float4 red[2 * kBlock];
+    extern __shared__ __align__(16) float4 fsm[];
     __shared__ uint32_t flag;
     ForceBody<MODE> b;
     b.p = prm;
-    b.shxy = shxy;
-    b.shzm = shzm;
-    b.red = red;
+    b.shxy = fsm;
+    b.shzm = fsm + 2 * kFTile;
+    b.red = fsm;
     b.flag = &flag;
     drive_ws(s, b);
 }
@@ -447,14 +464,51 @@ __global__ void __launch_bounds__(kBlock + 32) k_nbody_fd(FDParams prm, SchedArg
     drive_ws(s, b);
 }
 
-int occ(const void *fn)
+int occ(const void *fn, int block = kBlock + 32, size_t smem = 0)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock + 32, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
+}
+
+// Force kernels take kFSmem bytes of dynamic shared memory, above the default
+// limit: the opt-in is a per-function attribute of the current device, set
+// before every occupancy query and launch (a cheap driver call).
+template <uint32_t MODE>
+bool force_smem_ok()
+{
+    return cudaFuncSetAttribute((const void *)k_nbody_force<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kFSmem) == cudaSuccess;
+}
+
+template <uint32_t MODE>
+int occ_force()
+{
+    if (!force_smem_ok<MODE>()) {
+        cudaGetLastError();
+        return 0;
+    }
+    return occ((const void *)k_nbody_force<MODE>, kFBlock + 32, kFSmem);
+}
+
+template <uint32_t MODE>
+ecl_status launch_force(const NBodyParams &p, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    if (!force_smem_ok<MODE>()) {
+        err = "cannot enable the force kernel's shared memory";
+        cudaGetLastError();
+        return ECL_ERR_CUDA;
+    }
+    k_nbody_force<MODE><<<c.grid, kFBlock + 32, kFSmem, c.stream>>>(p, s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
 }
 
 ecl_status launched(std::string &err)
@@ -549,11 +603,10 @@ ecl_status l_step(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.out_vel = a.buf<float4>(6);
     p.lws = c.lws;
     if (!force_ws(p, c, (const void *)k_nbody_force<NB_STEP>, err)) return ECL_ERR_CUDA;
-    k_nbody_force<NB_STEP><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
-    return launched(err);
+    return launch_force<NB_STEP>(p, s, c, err);
 }
 
-int o_step() { return occ((const void *)k_nbody_force<NB_STEP>); }
+int o_step() { return occ_force<NB_STEP>(); }
 
 // ---- nbody_acc: in_pos, bodies, esp_sqr, out_acc
 ecl_status v_acc(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
@@ -576,11 +629,10 @@ ecl_status l_acc(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.out_acc = a.buf<float4>(3);
     p.lws = c.lws;
     if (!force_ws(p, c, (const void *)k_nbody_force<NB_ACC>, err)) return ECL_ERR_CUDA;
-    k_nbody_force<NB_ACC><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
-    return launched(err);
+    return launch_force<NB_ACC>(p, s, c, err);
 }
 
-int o_acc() { return occ((const void *)k_nbody_force<NB_ACC>); }
+int o_acc() { return occ_force<NB_ACC>(); }
 
 // ---- nbody_adjoint: in_pos, bodies, esp_sqr, grad_E, out_grad
 ecl_status v_adj(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
@@ -608,11 +660,10 @@ ecl_status l_adj(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.out_grad = a.buf<float4>(4);
     p.lws = c.lws;
     if (!force_ws(p, c, (const void *)k_nbody_force<NB_ADJ>, err)) return ECL_ERR_CUDA;
-    k_nbody_force<NB_ADJ><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
-    return launched(err);
+    return launch_force<NB_ADJ>(p, s, c, err);
 }
 
-int o_adj() { return occ((const void *)k_nbody_force<NB_ADJ>); }
+int o_adj() { return occ_force<NB_ADJ>(); }
 
 // ---- nbody_energy: in_pos, bodies, esp_sqr, out_energy (double[1]); workspace: G partials + counter
 ecl_status v_energy(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
@@ -696,20 +747,20 @@ extern const KernelDesc kNBody = {
     "nbody", 7,
     {{"in_pos", A_BUF_IN}, {"in_vel", A_BUF_IN}, {"bodies", A_I32}, {"del_t", A_F32}, {"esp_sqr", A_F32},
      {"out_pos", A_BUF_OUT}, {"out_vel", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_step, grain1, nchunks_force<2>, o_step, l_step,
+    1, 1, kFBlock + 32, 0, v_step, grain1, nchunks_force<2>, o_step, l_step,
 };
 
 extern const KernelDesc kNBodyAcc = {
     "nbody_acc", 4,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"out_acc", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_acc, grain1, nchunks_force<1>, o_acc, l_acc,
+    1, 1, kFBlock + 32, 0, v_acc, grain1, nchunks_force<1>, o_acc, l_acc,
 };
 
 extern const KernelDesc kNBodyAdjoint = {
     "nbody_adjoint", 5,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"grad_E", A_BUF_IN},
      {"out_grad", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_adj, grain1, nchunks_force<1>, o_adj, l_adj,
+    1, 1, kFBlock + 32, 0, v_adj, grain1, nchunks_force<1>, o_adj, l_adj,
 };
 
 extern const KernelDesc kNBodyEnergy = {

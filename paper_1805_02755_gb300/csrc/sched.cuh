@@ -136,6 +136,40 @@ __device__ Claim claim_chunks(const SchedArgs &s, const typename Body::Params &b
         c.nchunks = pk.nchunks;
         return c;
     }
+    if (s.mode == MODE_STATIC && !s.coverage) {
+        // Static: device d's package is table entry d, fixed before the launch,
+        // so a claim is one atomic on the device's chunk counter and no CTA
+        // waits for an election.  The claimer of chunk 0 stamps the record (t1
+        // is a running maximum of chunk end times, so it is left alone).
+        if (d >= s.npkg) {
+            c.done = 1;
+            return c;
+        }
+        const Pkg pk = s.table[d];
+        const uint32_t t = (uint32_t)atomicAdd(&s.dev[d].word, 1ull);
+        if (t >= pk.nchunks) {
+            c.done = 1;
+            return c;
+        }
+        if (t == 0) {
+            PkgRec *r = s.rec + d;
+            r->off = pk.off;
+            r->len = pk.len;
+            r->t0 = gtime();
+            r->pkg = d;
+            r->device = d;
+            r->cta = blockIdx.x;
+            r->smid = smid();
+            r->nchunks = pk.nchunks;
+        }
+        c.off = pk.off;
+        c.len = pk.len;
+        c.pkg = d;
+        c.t_begin = t;
+        c.t_end = t + 1;
+        c.nchunks = pk.nchunks;
+        return c;
+    }
     uint32_t spins = 0;
     for (;;) {
         const unsigned long long w = atomicAdd(&s.dev[d].word, 1ull);
@@ -302,21 +336,24 @@ __device__ __forceinline__ void sbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait on phase `parity`; false (and the queue's error word set)
-// when it gave up after about two seconds.  Each try_wait carries a suspend
-// hint, so a waiting thread sleeps until the phase completes (or the hint
-// runs out) instead of spinning: the scheduler warp waits out a whole chunk
-// this way and must not take issue slots from the compute warps.
-__device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsigned int *gerr)
+// when it gave up after about two seconds.  Between polls the thread sleeps
+// with a doubling back-off of up to max_sleep_ns: a waiting warp must not
+// take issue slots from the compute warps (the scheduler warp waits out a
+// whole chunk here; measured, a polling loop added a quarter to the
+// instructions of a force run).
+__device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsigned int *gerr,
+                                          uint32_t max_sleep_ns)
 {
     uint64_t t0 = 0;
+    uint32_t ns = 32;
     for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             "selp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
-            : "r"(sh_addr(bar)), "r"(parity), "r"(100000u)
+            : "r"(sh_addr(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
         const uint64_t now = gtime();
@@ -325,6 +362,8 @@ __device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsign
             atomicExch(gerr, (unsigned int)ECL_ERR_TIMEOUT);
             return false;
         }
+        __nanosleep(ns);
+        if (ns < max_sleep_ns) ns <<= 1;
     }
 }
 
@@ -361,14 +400,22 @@ __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // Loop state of thread 0 lives in shared memory and the claim is read from
+    // its ring slot when needed: registers held across body.run would come out
+    // of the body's budget (measured: a register copy of the claim and 64-bit
+    // timers cost a force run a quarter more instructions).
+    __shared__ uint64_t st_ts, st_first, st_last, st_busy;
+    __shared__ uint32_t st_n;
+    if (threadIdx.x == 0) {
+        st_first = st_last = st_busy = 0;
+        st_n = 0;
+    }
     __syncthreads();
-    uint64_t t_first = 0, t_last = 0, busy = 0;
-    uint32_t nchunks_done = 0;
     if (threadIdx.x >= NC) {
         if (threadIdx.x == NC) {  // scheduler: lane 0 of the last warp
             for (uint32_t i = 0;; ++i) {
                 const uint32_t r = i & 1;
-                if (!sbar_wait(&empty[r], ((i >> 1) & 1) ^ 1, gerr)) break;
+                if (!sbar_wait(&empty[r], ((i >> 1) & 1) ^ 1, gerr, 4096)) break;
                 Claim c = (*(volatile unsigned int *)gerr) ? Claim{} : claim_chunks<Body>(s, body.p, d);
                 if (*(volatile unsigned int *)gerr) c.done = 1;
                 ring[r] = c;
@@ -379,40 +426,43 @@ __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
     } else {
         for (uint32_t i = 0;; ++i) {
             const uint32_t r = i & 1;
-            if (threadIdx.x == 0) flag = sbar_wait(&full[r], (i >> 1) & 1, gerr) ? 0u : 1u;
+            if (threadIdx.x == 0) flag = sbar_wait(&full[r], (i >> 1) & 1, gerr, 256) ? 0u : 1u;
             body_sync(NC);
-            if (flag) break;
-            const Claim c = ring[r];
-            if (c.done) break;
-            uint64_t ts = 0;
-            if (threadIdx.x == 0) ts = gtime();
-            for (uint32_t t = c.t_begin; t < c.t_end; ++t) body.run(c.off, c.len, t, c.nchunks);
-            body_sync(NC);  // all compute threads are done with the chunk and the slot
+            if (flag || ring[r].done) break;
+            if (threadIdx.x == 0) st_ts = gtime();
+            const uint32_t tb = ring[r].t_begin, tz = ring[r].t_end;
+            for (uint32_t t = tb; t < tz; ++t) body.run(ring[r].off, ring[r].len, t, ring[r].nchunks);
+            body_sync(NC);  // all compute threads are done with the chunk
             if (threadIdx.x == 0) {
-                sbar_arrive(&empty[r]);
                 const uint64_t te = gtime();
-                if (!t_first) t_first = ts;
-                t_last = te;
-                busy += te - ts;
-                nchunks_done += c.t_end - c.t_begin;
+                if (!st_first) st_first = st_ts;
+                st_last = te;
+                st_busy += te - st_ts;
+                st_n += tz - tb;
                 if (!s.coverage) {
-                    finish_chunks_async(s, c.pkg, te);
+                    finish_chunks_async(s, ring[r].pkg, te);
+                    sbar_arrive(&empty[r]);  // the slot is no longer read
                     flag = 0;
                 } else {
-                    flag = finish_chunks(s, c.pkg, c.t_end - c.t_begin, c.nchunks, te) ? 1u : 0u;
+                    flag = finish_chunks(s, ring[r].pkg, tz - tb, ring[r].nchunks, te) ? 1u : 0u;
                 }
             }
             if (s.coverage) {  // debug: count every work-group of a finished package
                 body_sync(NC);
-                if (flag)
-                    for (uint64_t w = c.off + threadIdx.x; w < c.off + c.len; w += NC) atomicAdd(&s.coverage[w], 1u);
+                if (flag) {
+                    const uint64_t o = ring[r].off, z = ring[r].off + ring[r].len;
+                    for (uint64_t w = o + threadIdx.x; w < z; w += NC) atomicAdd(&s.coverage[w], 1u);
+                }
                 body_sync(NC);
-                if (threadIdx.x == 0) flag = 0;
+                if (threadIdx.x == 0) {
+                    flag = 0;
+                    sbar_arrive(&empty[r]);
+                }
             }
         }
     }
     __syncthreads();
-    exit_protocol(s, d, t_first, t_last, busy, nchunks_done, &flag);
+    exit_protocol(s, d, st_first, st_last, st_busy, st_n, &flag);
 }
 
 }  // namespace ecl
