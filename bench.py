@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 SMALL = False  # --small: reduced sizes for profiler captures (never a bench value)
+
+# ncu-measured DRAM bytes per launch of the dominant kernel (null once the kernel changes)
+NCU_TRAFFIC = {
+    "binomial": {"bytes_per_launch": 759.04e3 * 64,
+                 "source": "profiles/binomial_greeks_16384_options.md (16384 options x 64)"},
+}
 METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
 L2_FLUSH_BYTES = 512 << 20
 SMS_NOMINAL = 152
@@ -676,7 +682,13 @@ def run_ours(args):
     value = total_wi * world / (step_ms * 1e-3)
     rf = dict(kern[dominant]["roofline"])
     rf["kernel"] = dominant
-    rf["traffic"] = None
+    # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+    # committed ncu summary of the current kernel; small-case captures are scaled to a
+    # full launch by the units processed (the traffic is per option)
+    t = NCU_TRAFFIC.get(dominant)
+    rf["traffic"] = None if (t is None or SMALL) else t["bytes_per_launch"]
+    if t is not None and not SMALL:
+        rf["traffic_source"] = t["source"]
     rf["peak_source"] = peaks["src"] if rf["bound"] not in ("alu", "mufu") else \
         "derived: %d SMs x %d lanes x %.0f MHz (max SM clock); FP32 pipe measured 127 FMA/clk/SM" % (
             sms, 128 if rf["bound"] == "alu" else 16, peaks["sm_max_mhz"])
