@@ -362,7 +362,11 @@ void ecl_oracle_bf16_round_array(const float *in, float *out, int64_t n)
  *   mode 1: A * B in FP64 of the FP32 inputs (the compensated mode's target)
  *   mode 2: hi(A)hi(B) + hi(A)lo(B) + lo(A)hi(B) with hi = bf16(x),
  *           lo = bf16(x - hi) (FP32 subtraction): the three-product split's
- *           exact value. */
+ *           exact value.
+ *   mode 3: the six-product split: x = h + m + l with h = bf16(x),
+ *           m = bf16(x - h), l = bf16((x - h) - m) (FP32 subtractions), and
+ *           C = hh + hm + mh + hl + lh + mm (the products of order up to
+ *           2^-16 relative; ml, lm and ll are left out). */
 void ecl_oracle_gemm_entries(const float *A, const float *Bt, int64_t M, int64_t N,
                              int64_t K, int32_t mode, const int64_t *ii,
                              const int64_t *jj, int64_t count, double *out)
@@ -378,6 +382,17 @@ void ecl_oracle_gemm_entries(const float *A, const float *Bt, int64_t M, int64_t
                 s += (double)ecl_oracle_bf16_round(a[k]) * (double)ecl_oracle_bf16_round(b[k]);
             } else if (mode == 1) {
                 s += (double)a[k] * (double)b[k];
+            } else if (mode == 3) {
+                const float ah = ecl_oracle_bf16_round(a[k]);
+                const float ar = a[k] - ah;
+                const float am = ecl_oracle_bf16_round(ar);
+                const float al = ecl_oracle_bf16_round(ar - am);
+                const float bh = ecl_oracle_bf16_round(b[k]);
+                const float br = b[k] - bh;
+                const float bm = ecl_oracle_bf16_round(br);
+                const float bl = ecl_oracle_bf16_round(br - bm);
+                s += (double)ah * (double)bh + (double)ah * (double)bm + (double)am * (double)bh +
+                     (double)ah * (double)bl + (double)al * (double)bh + (double)am * (double)bm;
             } else {
                 const float ah = ecl_oracle_bf16_round(a[k]);
                 const float al = ecl_oracle_bf16_round(a[k] - ah);

@@ -353,3 +353,47 @@ def test_gemm_split3_error_model(oracle_mod):
     e2 = np.linalg.norm(oracle_mod.gemm(A, Bt, 2) - exact) / np.linalg.norm(exact)
     assert 1e-4 < e0 < 1e-2
     assert e2 < 2e-5
+
+
+def test_gemm_split6_worked_value(oracle_mod):
+    # x = 1 + 2^-10 + 2^-20 splits into h = 1, m = 2^-10, l = 2^-20 (each a bf16);
+    # the six products give x^2 minus exactly the dropped 2ml + l^2 = 2^-29 + 2^-40
+    x = np.array([[1.0 + 2 ** -10 + 2 ** -20]], dtype=np.float32)
+    assert float(x[0, 0]) == 1.0 + 2 ** -10 + 2 ** -20
+    c6 = oracle_mod.gemm(x, x, 3)[0, 0]
+    c1 = oracle_mod.gemm(x, x, 1)[0, 0]
+    assert c1 - c6 == 2.0 ** -29 + 2.0 ** -40
+    assert c6 == 1.0 + 2.0 ** -9 + 2.0 ** -19 + 2.0 ** -20
+
+
+def test_gemm_split6_split_is_exact(oracle_mod):
+    # with Bt = [[1]] the six products reduce to h + m + l, which must equal x
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.standard_normal(4000), rng.standard_normal(1000) * 1e20,
+                        rng.standard_normal(1000) * 1e-20]).astype(np.float32).reshape(-1, 1)
+    one = np.ones((1, 1), dtype=np.float32)
+    got = oracle_mod.gemm(x, one, 3)[:, 0]
+    assert np.array_equal(got, x[:, 0].astype(np.float64))
+
+
+def test_gemm_split6_bf16_inputs_are_exact(oracle_mod):
+    # inputs that are already bf16 have m = l = 0: all modes give the same exact product
+    A, Bt = W.gemm_matrices(12, 10, 24, seed=34)
+    A = oracle_mod.bf16_round(A)
+    Bt = oracle_mod.bf16_round(Bt)
+    c1 = oracle_mod.gemm(A, Bt, 1)
+    assert np.array_equal(oracle_mod.gemm(A, Bt, 3), c1)
+    assert np.array_equal(oracle_mod.gemm(A, Bt, 0), c1)
+
+
+def test_gemm_split6_error_bound(oracle_mod):
+    # |m| <= 2^-8 |x| and |l| <= 2^-16 |x| (round to nearest twice), so the dropped
+    # ml + lm + ll are at most 2^-23 |a||b| per term; far below the split-3 error
+    A, Bt = W.gemm_matrices(32, 32, 256, seed=35)
+    exact = oracle_mod.gemm(A, Bt, 1)
+    c6 = oracle_mod.gemm(A, Bt, 3)
+    absprod = np.abs(A.astype(np.float64)) @ np.abs(Bt.astype(np.float64)).T
+    assert np.all(np.abs(c6 - exact) <= 2.0 ** -23 * absprod)
+    e6 = np.linalg.norm(c6 - exact) / np.linalg.norm(exact)
+    e2 = np.linalg.norm(oracle_mod.gemm(A, Bt, 2) - exact) / np.linalg.norm(exact)
+    assert e6 < 1e-7 and e6 < e2 / 100
