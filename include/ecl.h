@@ -357,6 +357,19 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   into hi = bf16(x) and lo = bf16(x - hi); C = A_hi B_hi + A_hi B_lo +
  *   A_lo B_hi in one FP32 accumulator.  Uses an engine-owned workspace.
  *
+ * "gemm_split6"  (7 args; lws 16384 = one 128 x 128 output tile; the
+ *   scheduling unit is one row of tiles)  A, Bt, C, M, N, K as "gemm_split3"
+ *   (A, Bt float) plus 6 S int32 chunk_k (0 = 1).  Not in the paper: the
+ *   compensated GEMM carried to FP32 accuracy.  Each input is split into
+ *   x = h + m + l, h = bf16(x), m = bf16(x - h), l = bf16(x - h - m), and
+ *   C = hh + (hm + mh + hl + lh + mm): the hh products go into a fresh
+ *   tensor-memory accumulator for every chunk_k slices of 64 along K and
+ *   are added into FP32 registers (round to nearest) after each chunk; the
+ *   five cross products accumulate over the whole K and are added once.
+ *   gws = ceil(M/128) * ceil(N/128) * 16384; K % 8 == 0; A and Bt need no
+ *   alignment (they are read by the split pass), C 16-byte aligned.  Uses
+ *   an engine-owned workspace of 6 bf16 copies (12 * (M + N) * K bytes).
+ *
  * "cast_bf16"  (3 args, 1:1, any lws)  0 B in float[n]  1 B out bf16[n]
  *   2 S int64 n: round to nearest even (the input cast of "gemm_bf16").
  */

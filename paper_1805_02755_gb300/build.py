@@ -31,8 +31,9 @@ SOURCES = {
     "k_nbody.cu": ["-ftz=true"],
     "k_binomial.cu": [],
     "k_gemm.cu": [],
+    "k_gemm6.cu": [],
 }
-HEADERS = ["ecl_internal.h", "sched.cuh", "f32x2.cuh"]
+HEADERS = ["ecl_internal.h", "sched.cuh", "f32x2.cuh", "tc.cuh"]
 
 
 def nvcc() -> str:

@@ -17,6 +17,7 @@ extern const KernelDesc kBinomial;
 extern const KernelDesc kBinomialBatch;
 extern const KernelDesc kGemmBF16;
 extern const KernelDesc kGemmSplit3;
+extern const KernelDesc kGemmSplit6;
 extern const KernelDesc kCastBF16;
 
 static const KernelDesc *const kAll[] = {
@@ -31,6 +32,7 @@ static const KernelDesc *const kAll[] = {
     &kBinomialBatch,
     &kGemmBF16,
     &kGemmSplit3,
+    &kGemmSplit6,
     &kCastBF16,
 };
 
