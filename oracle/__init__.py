@@ -69,6 +69,7 @@ def lib():
             L.ecl_oracle_bf16_round.restype = _f32
             L.ecl_oracle_bf16_round_array.argtypes = [_p, _p, _i64]
             L.ecl_oracle_gemm_entries.argtypes = [_p, _p, _i64, _i64, _i64, _i32, _p, _p, _i64, _p]
+            L.ecl_oracle_ray.argtypes = [_p, _i32, _i32, _i64, _i64, _f32, _f32, _f32, _f32, _i32, _p, _i64, _i64]
             _lib = L
     return _lib
 
@@ -283,3 +284,18 @@ def gemm(A: np.ndarray, Bt: np.ndarray, mode: int, threads: Optional[int] = None
     N = Bt.shape[0]
     ii, jj = np.meshgrid(np.arange(M), np.arange(N), indexing="ij")
     return gemm_entries(A, Bt, mode, ii.ravel(), jj.ravel(), threads).reshape(M, N)
+
+
+# ---------------------------------------------------------------- Ray
+def ray(scene: np.ndarray, nspheres: int, nlights: int, width: int, height: int, ka: float, bg, max_depth: int,
+        rows=None, threads: Optional[int] = None) -> np.ndarray:
+    """Whitted ray tracer in FP32 (see oracle.c): (height, width, 4) = r, g, b, rays traced."""
+    L = lib()
+    scene = _c(scene, np.float32)
+    assert scene.size >= 12 * nspheres + 8 * nlights
+    out = np.zeros((height, width, 4), dtype=np.float32)
+    b, e = rows if rows is not None else (0, height)
+    _run(lambda r0, r1: L.ecl_oracle_ray(_ptr(scene), nspheres, nlights, width, height, np.float32(ka),
+                                         np.float32(bg[0]), np.float32(bg[1]), np.float32(bg[2]), max_depth,
+                                         _ptr(out), r0, r1), b, e, threads)
+    return out

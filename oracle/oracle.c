@@ -404,3 +404,166 @@ void ecl_oracle_gemm_entries(const float *A, const float *Bt, int64_t M, int64_t
         out[t] = s;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Ray tracing (Sec. 7 "Ray": an irregular ray tracer over a scene of
+ * spheres and point lights; Table 2: lws 128, scene in / image out, 1:1).
+ * The paper's ray tracer and scenes are not available, so the method here
+ * is a plain Whitted tracer, evaluated in FP32 operation by operation (no
+ * fused multiply-add) so that a GPU evaluation in the same order matches
+ * bit for bit.
+ *
+ * Scene (floats): sphere k at s[12k..]: centre x y z, radius, colour r g b,
+ * reflectivity, kd, ks, log2 of the specular exponent, pad; light l after
+ * the spheres at L[8l..]: position x y z, pad, intensity r g b, pad.
+ * Camera at the origin looking down -z: pixel (i, j) has direction
+ * (u, v, -1) / |(u, v, -1)| with u = (2i + 1 - W) / H, v = (H - 2j - 1) / H.
+ * A ray's nearest hit is the smallest t > eps over the spheres in index
+ * order (the first of equal t wins).  At a hit p with normal
+ * n = (p - c) / |p - c| (normalised, so a grazing hit that rounding puts off
+ * the surface still shades with a unit normal):
+ *   local = ka col + sum over lights not shadowed (a shadow ray from
+ *   p + eps n towards the light hits a sphere before it) of
+ *   kd (n.l) col I  [n.l > 0]  +  ks (r.(-d))^(2^e) I  [r.(-d) > 0],
+ *   r = 2 (n.l) n - l.
+ * Reflections are followed front to back: with weight w (1 at first),
+ * colour += w (1 - refl) local and w *= refl while refl > 0 and the depth
+ * is below max_depth (the ray continues from p + eps n along the unit
+ * vector of d - 2 (d.n) n); otherwise colour += w local and the ray ends; a miss adds
+ * w * background.  Output per pixel: r, g, b, and the number of rays traced
+ * (camera, reflected and shadow rays) as a float. */
+#define RAY_EPS 1e-3f
+
+static int ray_nearest(const float *sph, int32_t ns, float ox, float oy, float oz, float dx, float dy,
+                       float dz, float *t_out)
+{
+    int best = -1;
+    float tb = 3.0e38f;
+    for (int32_t k = 0; k < ns; ++k) {
+        const float *s = sph + 12 * k;
+        const float ocx = ox - s[0], ocy = oy - s[1], ocz = oz - s[2];
+        const float b = ocx * dx + ocy * dy + ocz * dz;
+        const float c = (ocx * ocx + ocy * ocy + ocz * ocz) - s[3] * s[3];
+        const float disc = b * b - c;
+        if (disc < 0.0f) continue;
+        const float sq = sqrtf(disc);
+        float t = -b - sq;
+        if (!(t > RAY_EPS)) t = -b + sq;
+        if (t > RAY_EPS && t < tb) {
+            tb = t;
+            best = (int)k;
+        }
+    }
+    *t_out = tb;
+    return best;
+}
+
+static int ray_blocked(const float *sph, int32_t ns, float ox, float oy, float oz, float dx, float dy, float dz,
+                       float dist)
+{
+    for (int32_t k = 0; k < ns; ++k) {
+        const float *s = sph + 12 * k;
+        const float ocx = ox - s[0], ocy = oy - s[1], ocz = oz - s[2];
+        const float b = ocx * dx + ocy * dy + ocz * dz;
+        const float c = (ocx * ocx + ocy * ocy + ocz * ocz) - s[3] * s[3];
+        const float disc = b * b - c;
+        if (disc < 0.0f) continue;
+        const float sq = sqrtf(disc);
+        float t = -b - sq;
+        if (!(t > RAY_EPS)) t = -b + sq;
+        if (t > RAY_EPS && t < dist) return 1;
+    }
+    return 0;
+}
+
+void ecl_oracle_ray(const float *scene, int32_t ns, int32_t nl, int64_t width, int64_t height, float ka,
+                    float bg_r, float bg_g, float bg_b, int32_t max_depth, float *out, int64_t row_begin,
+                    int64_t row_end)
+{
+    const float *lights = scene + 12 * (int64_t)ns;
+    const float inv = 1.0f / (float)height;
+    for (int64_t j = row_begin; j < row_end; ++j) {
+        for (int64_t i = 0; i < width; ++i) {
+            const float u = (float)(2 * i + 1 - width) * inv;
+            const float v = (float)(height - 2 * j - 1) * inv;
+            const float len = sqrtf(u * u + v * v + 1.0f);
+            float dx = u / len, dy = v / len, dz = -1.0f / len;
+            float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+            float cr = 0.0f, cg = 0.0f, cb = 0.0f, w = 1.0f;
+            int32_t rays = 1;
+            for (int32_t depth = 0;; ++depth) {
+                float t;
+                const int k = ray_nearest(scene, ns, ox, oy, oz, dx, dy, dz, &t);
+                if (k < 0) {
+                    cr += w * bg_r;
+                    cg += w * bg_g;
+                    cb += w * bg_b;
+                    break;
+                }
+                const float *s = scene + 12 * k;
+                const float px = ox + t * dx, py = oy + t * dy, pz = oz + t * dz;
+                const float qx = px - s[0], qy = py - s[1], qz = pz - s[2];
+                const float ql = sqrtf(qx * qx + qy * qy + qz * qz);
+                const float nx = qx / ql, ny = qy / ql, nz = qz / ql;
+                const float sox = px + nx * RAY_EPS, soy = py + ny * RAY_EPS, soz = pz + nz * RAY_EPS;
+                float lr = ka * s[4], lg = ka * s[5], lb = ka * s[6];
+                const int32_t e = (int32_t)s[10];
+                for (int32_t l = 0; l < nl; ++l) {
+                    const float *L = lights + 8 * l;
+                    float lx = L[0] - px, ly = L[1] - py, lz = L[2] - pz;
+                    const float dist = sqrtf(lx * lx + ly * ly + lz * lz);
+                    lx = lx / dist;
+                    ly = ly / dist;
+                    lz = lz / dist;
+                    ++rays;
+                    if (ray_blocked(scene, ns, sox, soy, soz, lx, ly, lz, dist)) continue;
+                    const float ndl = nx * lx + ny * ly + nz * lz;
+                    if (!(ndl > 0.0f)) continue;
+                    const float dif = s[8] * ndl;
+                    lr += (dif * s[4]) * L[4];
+                    lg += (dif * s[5]) * L[5];
+                    lb += (dif * s[6]) * L[6];
+                    const float rx = (2.0f * ndl) * nx - lx, ry = (2.0f * ndl) * ny - ly,
+                                rz = (2.0f * ndl) * nz - lz;
+                    const float rdv = -(rx * dx + ry * dy + rz * dz);
+                    if (rdv > 0.0f) {
+                        float sp = rdv;
+                        for (int32_t q = 0; q < e; ++q) sp = sp * sp;
+                        const float spec = s[9] * sp;
+                        lr += spec * L[4];
+                        lg += spec * L[5];
+                        lb += spec * L[6];
+                    }
+                }
+                const float refl = s[7];
+                if (refl > 0.0f && depth < max_depth) {
+                    const float wl = w * (1.0f - refl);
+                    cr += wl * lr;
+                    cg += wl * lg;
+                    cb += wl * lb;
+                    w = w * refl;
+                    const float dn = dx * nx + dy * ny + dz * nz;
+                    const float rx = dx - (2.0f * dn) * nx, ry = dy - (2.0f * dn) * ny, rz = dz - (2.0f * dn) * nz;
+                    const float rl = sqrtf(rx * rx + ry * ry + rz * rz);
+                    dx = rx / rl;
+                    dy = ry / rl;
+                    dz = rz / rl;
+                    ox = sox;
+                    oy = soy;
+                    oz = soz;
+                    ++rays;
+                } else {
+                    cr += w * lr;
+                    cg += w * lg;
+                    cb += w * lb;
+                    break;
+                }
+            }
+            float *o = out + 4 * (j * width + i);
+            o[0] = cr;
+            o[1] = cg;
+            o[2] = cb;
+            o[3] = (float)rays;
+        }
+    }
+}

@@ -14,6 +14,9 @@ shapes, sizes and value distributions of the five configurations:
                   U[0.25,2], volatility U[0.1,0.5], depth N uniform integer in
                   [256, 2048], rate 0.02.
 * GEMM         -- A (M x K) and B stored transposed (N x K), N(0,1) FP32.
+* Ray          -- a seeded scene (the paper's scenes are not available): a
+                  large ground sphere, spheres scattered in front of the
+                  camera (40% reflective), three point lights; sky above.
 
 This module holds none of the method's arithmetic; the oracle and the CUDA
 path both take these arrays as they are.  Every generator is a pure function
@@ -84,3 +87,35 @@ def gemm_matrices(M: int, N: int, K: int, seed: int = SEED_BASE + 4):
     A = g.standard_normal((M, K), dtype=np.float32)
     Bt = g.standard_normal((N, K), dtype=np.float32)
     return A, Bt
+
+
+# ---------------------------------------------------------------- Ray
+RAY_SPHERE_FLOATS = 12  # x y z r | colour r g b | reflectivity kd ks log2(spec exponent) | pad
+RAY_LIGHT_FLOATS = 8    # x y z pad | intensity r g b pad
+
+
+def ray_scene(nspheres: int = 64, nlights: int = 3, seed: int = SEED_BASE + 5) -> dict:
+    """Scene buffer (spheres then lights, float32) and the tracer's scalars."""
+    g = rng(seed)
+    sph = np.zeros((nspheres, RAY_SPHERE_FLOATS), dtype=np.float64)
+    if nspheres > 0:  # the ground: a large, slightly reflective sphere
+        sph[0] = [0.0, -1001.0, -10.0, 1000.0, 0.6, 0.6, 0.55, 0.2, 0.8, 0.1, 2.0, 0.0]
+    for k in range(1, nspheres):
+        refl = 0.0 if g.random() < 0.6 else g.uniform(0.3, 0.9)
+        sph[k] = [g.uniform(-6.0, 6.0), g.uniform(-0.8, 3.0), g.uniform(-22.0, -6.0), g.uniform(0.3, 1.2),
+                  *g.uniform(0.2, 1.0, 3), refl, g.uniform(0.5, 0.9), g.uniform(0.1, 0.6),
+                  float(g.integers(3, 7)), 0.0]
+    pos = np.array([[-10.0, 10.0, 0.0], [10.0, 8.0, -5.0], [0.0, 20.0, -15.0]])
+    lig = np.zeros((nlights, RAY_LIGHT_FLOATS), dtype=np.float64)
+    for l in range(nlights):
+        lig[l, :3] = pos[l % 3] + (l // 3) * np.array([1.5, 0.5, -2.0])
+        lig[l, 4:7] = g.uniform(0.4, 0.8, 3)
+    scene = np.concatenate([sph.ravel(), lig.ravel()]).astype(np.float32)
+    return dict(scene=scene, nspheres=nspheres, nlights=nlights, ka=0.1, bg=(0.05, 0.07, 0.12), max_depth=3)
+
+
+def ray_scene_from(spheres, lights) -> np.ndarray:
+    """Scene buffer from explicit rows (lists of 12 and 8 numbers)."""
+    sph = np.asarray(spheres, dtype=np.float64).reshape(-1, RAY_SPHERE_FLOATS)
+    lig = np.asarray(lights, dtype=np.float64).reshape(-1, RAY_LIGHT_FLOATS)
+    return np.concatenate([sph.ravel(), lig.ravel()]).astype(np.float32)
