@@ -370,6 +370,23 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   alignment (they are read by the split pass), C 16-byte aligned.  Uses
  *   an engine-owned workspace of 6 bf16 copies (12 * (M + N) * K bytes).
  *
+ * "ray"  (11 args, out pattern 1:1; Table 2 gives lws 128)  Sec. 7's Ray
+ *   workload as a Whitted tracer (the paper's tracer and scenes are not
+ *   available, so the definition is this library's):
+ *     0 B scene float[12*spheres + 8*lights]: sphere k = centre x y z,
+ *       radius, colour r g b, reflectivity, kd, ks, log2 of the specular
+ *       exponent, pad; then light l = position x y z, pad, intensity r g b,
+ *       pad
+ *     1 S int32 spheres (0..256)  2 S int32 lights (0..16)  3 S int32 width
+ *     4 S int32 height  5 S float ambient  6-8 S float background r g b
+ *     9 S int32 max_depth (0..64)  10 B out float4[width*height]
+ *   Work-item g traces pixel g (row-major) from a camera at the origin
+ *   looking down -z (u = (2i+1-W)/H, v = (H-2j-1)/H): nearest sphere hit,
+ *   hard shadows from every light, Phong shading, mirror reflections
+ *   followed front to back while reflectivity > 0 and depth < max_depth.
+ *   out = (r, g, b, rays traced).  FP32 without fused multiply-add: the
+ *   result is bit-reproducible on the host.
+ *
  * "cast_bf16"  (3 args, 1:1, any lws)  0 B in float[n]  1 B out bf16[n]
  *   2 S int64 n: round to nearest even (the input cast of "gemm_bf16").
  */

@@ -2,8 +2,8 @@
 
 Each .cu file is compiled to an object in parallel, then the objects are
 linked into one shared library next to this file.  The Mandelbrot unit is
-compiled with -fmad=false (its counts must match a correctly rounded host
-evaluation bit for bit).  The NBody unit is compiled with -ftz=true: every
+and ray-tracing units are compiled with -fmad=false (their results must
+match a correctly rounded host evaluation bit for bit).  The NBody unit is compiled with -ftz=true: every
 FP32 value there is far from the subnormal range (r^2 >= eps^2 > 0), and
 without subnormal handling rsqrtf is the bare hardware reciprocal square
 root instead of a range check, a scaling and the root.
@@ -32,6 +32,7 @@ SOURCES = {
     "k_binomial.cu": [],
     "k_gemm.cu": [],
     "k_gemm6.cu": [],
+    "k_ray.cu": ["-fmad=false"],
 }
 HEADERS = ["ecl_internal.h", "sched.cuh", "f32x2.cuh", "tc.cuh"]
 

@@ -19,6 +19,7 @@ extern const KernelDesc kGemmBF16;
 extern const KernelDesc kGemmSplit3;
 extern const KernelDesc kGemmSplit6;
 extern const KernelDesc kCastBF16;
+extern const KernelDesc kRay;
 
 static const KernelDesc *const kAll[] = {
     &kMandelbrot,
@@ -34,6 +35,7 @@ static const KernelDesc *const kAll[] = {
     &kGemmSplit3,
     &kGemmSplit6,
     &kCastBF16,
+    &kRay,
 };
 
 const KernelDesc *find_kernel(const char *name)

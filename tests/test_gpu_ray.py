@@ -1,0 +1,107 @@
+"""Ray workload through the C ABI vs the FP32 oracle: bit-exact colours and ray counts.
+
+Both sides evaluate the same definition in FP32 without fused multiply-add, in
+the same operation order, with IEEE division and square root, so every pixel
+must match exactly under every scheduler.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1805_02755_gb300 import build as B
+    B.build()
+    import paper_1805_02755_gb300 as E
+    return E
+
+
+def run_ray(E, sc, Wd, Hd, lws=128, sched="hguided", params=(2.0, 1.0), D=0, C=0, coverage=False, ns=None,
+            nl=None, depth=None):
+    import torch
+    ns = sc["nspheres"] if ns is None else ns
+    nl = sc["nlights"] if nl is None else nl
+    depth = sc["max_depth"] if depth is None else depth
+    scene = torch.from_numpy(sc["scene"]).cuda()
+    out = torch.full((Wd * Hd + 4, 4), -7.0, device="cuda")
+    G = -(-Wd * Hd // lws)
+    cov = torch.zeros(G, dtype=torch.int32, device="cuda") if coverage else None
+    eng = E.Engine(0)
+    p = E.Program("ray").in_(scene).out(out).args(scene, ns, nl, Wd, Hd, sc["ka"], *sc["bg"], depth, out)
+    eng.work_items(G * lws, lws).scheduler(sched, params).workers(D, C).program(p)
+    eng.set_coverage(cov)
+    eng.run().synchronize()
+    o = out.cpu().numpy()
+    assert (o[Wd * Hd:] == -7.0).all(), "wrote past the image"
+    eng.close()
+    return o[: Wd * Hd].reshape(Hd, Wd, 4), cov
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return W.ray_scene()
+
+
+@pytest.mark.parametrize("Wd,Hd,lws", [(96, 64, 128), (37, 23, 128), (1, 1, 128), (130, 130, 96), (200, 120, 256)])
+def test_ray_bit_exact(E, oracle_mod, scene, Wd, Hd, lws):
+    got, _ = run_ray(E, scene, Wd, Hd, lws)
+    ref = oracle_mod.ray(scene["scene"], scene["nspheres"], scene["nlights"], Wd, Hd, scene["ka"], scene["bg"],
+                         scene["max_depth"])
+    assert np.array_equal(got, ref), np.argwhere(got != ref)[:5]
+
+
+@pytest.mark.parametrize("sched,params,D,C", [("static", (), 1, 0), ("static_rev", (0.3, 0.3), 3, 0),
+                                              ("dynamic", (17,), 4, 0), ("hguided", (2.0, 1.0), 8, 0),
+                                              ("hguided", (1.0, 2.0, 1.0, 3.0), 2, 0), ("monolithic", (), 0, 0)])
+def test_ray_schedulers(E, oracle_mod, scene, sched, params, D, C):
+    Wd, Hd = 160, 96
+    got, cov = run_ray(E, scene, Wd, Hd, 128, sched, params, D, C, coverage=(sched != "monolithic"))
+    ref = oracle_mod.ray(scene["scene"], scene["nspheres"], scene["nlights"], Wd, Hd, scene["ka"], scene["bg"],
+                         scene["max_depth"])
+    assert np.array_equal(got, ref)
+    if cov is not None:
+        assert (cov.cpu().numpy() == 1).all()
+
+
+@pytest.mark.parametrize("ns,nl,depth", [(0, 3, 3), (64, 0, 3), (64, 3, 0), (1, 1, 1)])
+def test_ray_degenerate_scenes(E, oracle_mod, scene, ns, nl, depth):
+    Wd, Hd = 48, 40
+    # a sub-scene: the first ns spheres and the first nl lights
+    sph = scene["scene"][: 12 * scene["nspheres"]].reshape(-1, 12)[:ns]
+    lig = scene["scene"][12 * scene["nspheres"]:].reshape(-1, 8)[:nl]
+    sub = dict(scene, scene=W.ray_scene_from(sph, lig), nspheres=ns, nlights=nl, max_depth=depth)
+    got, _ = run_ray(E, sub, Wd, Hd)
+    ref = oracle_mod.ray(sub["scene"], ns, nl, Wd, Hd, sub["ka"], sub["bg"], depth)
+    assert np.array_equal(got, ref)
+
+
+def test_ray_rejects_bad_arguments(E, scene):
+    import torch
+    s = torch.from_numpy(scene["scene"]).cuda()
+    out = torch.zeros((64 * 64, 4), device="cuda")
+    for ns, nl, Wd, depth, lws in [(300, 3, 64, 3, 128), (64, 20, 64, 3, 128), (64, 3, 0, 3, 128),
+                                   (64, 3, 64, -1, 128), (64, 3, 64, 3, 2048)]:
+        eng = E.Engine(0)
+        p = E.Program("ray").in_(s).out(out).args(s, ns, nl, Wd, 64, 0.1, 0.0, 0.0, 0.0, depth, out)
+        eng.work_items(64 * 64 if lws <= 1024 else 2048 * 2, lws).scheduler("dynamic", (8,)).program(p)
+        with pytest.raises(E.EclError):
+            eng.run()
+        eng.close()
+
+
+def test_ray_full_size_sampled_rows(E, oracle_mod, scene):
+    Wd = Hd = 2048
+    got, _ = run_ray(E, scene, Wd, Hd)
+    rows = [0, 311, 700, 1023, 1024, 1500, 1900, 2047]
+    for r in rows:
+        ref = oracle_mod.ray(scene["scene"], scene["nspheres"], scene["nlights"], Wd, Hd, scene["ka"], scene["bg"],
+                             scene["max_depth"], rows=(r, r + 1))
+        assert np.array_equal(got[r], ref[r]), r
+    rays = got[..., 3]
+    assert rays.min() == 1.0 and (rays == 1.0).mean() > 0.2  # sky and expensive regions both present
