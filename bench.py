@@ -478,9 +478,9 @@ class MultiEngine:
 class Ray(Workload):
     """The paper's fifth benchmark (Sec. 7 "Ray"), not one of the five measured
     configurations: a Whitted tracer over a seeded 64-sphere, 3-light scene at
-    2048 x 2048, HGuided over 8 devices; reported beside the step."""
+    2048 x 2048, HGuided over one device of one-warp CTAs; reported beside the step."""
     name = "ray"
-    sched = ("hguided", (2.0, 1.0), 8, 0)
+    sched = ("hguided", (2.0, 1.0), 1, 0)
     in_step = False
 
     def host_setup(self):
@@ -498,7 +498,7 @@ class Ray(Workload):
         self.h_in = [s.pin_memory()]
         self.h_out = [torch.zeros((self.gws, 4)).pin_memory()]
         self.config = dict(size="%dx%d" % (self.Wd, self.Hd), spheres=self.sc["nspheres"], lights=self.sc["nlights"],
-                           max_depth=self.sc["max_depth"], scheduler="hguided k=2 over 8 devices")
+                           max_depth=self.sc["max_depth"], scheduler="hguided k=2, one device")
 
     def program(self, ins, outs):
         sc = self.sc

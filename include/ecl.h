@@ -377,7 +377,7 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *       radius, colour r g b, reflectivity, kd, ks, log2 of the specular
  *       exponent, pad; then light l = position x y z, pad, intensity r g b,
  *       pad
- *     1 S int32 spheres (0..256)  2 S int32 lights (0..16)  3 S int32 width
+ *     1 S int32 spheres (0..128)  2 S int32 lights (0..16)  3 S int32 width
  *     4 S int32 height  5 S float ambient  6-8 S float background r g b
  *     9 S int32 max_depth (0..64)  10 B out float4[width*height]
  *   Work-item g traces pixel g (row-major) from a camera at the origin

@@ -9,9 +9,14 @@
 // root, so colours and ray counts match a host evaluation bit for bit.
 //
 // Work-item g traces pixel g of the row-major W x H image and writes one
-// float4 (r, g, b, rays traced).  One chunk = one work-group; the CTA's 128
-// compute threads stride over the work-group's pixels.  The scene (at most
-// 256 spheres and 16 lights) is staged in shared memory once per CTA:
+// float4 (r, g, b, rays traced).  One chunk = one work-group; a CTA is one
+// warp that strides over the work-group's pixels.  Pixel costs vary by an
+// order of magnitude (sky: one ray; reflective spheres: up to 16), so
+// workers are kept small: with 128-thread CTAs the warps of a chunk waited
+// for its most expensive pixels and the older CTAs on an SM out-ran the
+// younger ones, 23-45% slower than a monolithic launch against 6-8% with
+// one-warp CTAs (measured at 2048^2).  The scene (at most
+// 128 spheres and 16 lights) is staged in shared memory once per CTA:
 // sphere geometry as float4 (centre, r^2), materials separately.
 #include <cuda_runtime.h>
 
@@ -21,8 +26,8 @@
 namespace ecl {
 namespace {
 
-constexpr int kBlock = 128;
-constexpr int kMaxSpheres = 256;
+constexpr int kBlock = 32;
+constexpr int kMaxSpheres = 128;
 constexpr int kMaxLights = 16;
 constexpr float kEps = 1e-3f;
 
@@ -191,7 +196,7 @@ struct RayBody {
     }
 };
 
-__global__ void __launch_bounds__(kBlock + 32, 4) k_ray(RayParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kBlock, 24) k_ray(RayParams prm, SchedArgs s)
 {
     __shared__ RayScene sc;
     const float *lights = prm.scene + 12 * (int64_t)prm.ns;
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(kBlock + 32, 4) k_ray(RayParams prm, SchedArgs
     RayBody b;
     b.p = prm;
     b.sc = &sc;
-    drive_ws(s, b);
+    drive(s, b);
 }
 
 RayParams params_of(const KArgs &a, uint32_t lws)
@@ -235,7 +240,7 @@ ecl_status validate(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err
 {
     const int64_t ns = a.i32(1), nl = a.i32(2), W = a.i32(3), H = a.i32(4), depth = a.i32(9);
     if (ns < 0 || ns > kMaxSpheres || nl < 0 || nl > kMaxLights) {
-        err = "0..256 spheres and 0..16 lights";
+        err = "0..128 spheres and 0..16 lights";
         return ECL_ERR_ARG;
     }
     if (W <= 0 || H <= 0 || depth < 0 || depth > 64) {
@@ -271,7 +276,7 @@ uint32_t nchunks(const KArgs &a, uint64_t, uint32_t lws, uint64_t off, uint64_t 
 int ctas_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ray, kBlock + 32, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ray, kBlock, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -280,7 +285,7 @@ int ctas_per_sm()
 
 ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
-    k_ray<<<c.grid, kBlock + 32, 0, c.stream>>>(params_of(a, c.lws), s);
+    k_ray<<<c.grid, kBlock, 0, c.stream>>>(params_of(a, c.lws), s);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);
@@ -299,7 +304,7 @@ extern const KernelDesc kRay = {
      {"out", A_BUF_OUT}},
     1,
     1,
-    kBlock + 32,
+    kBlock,
     0,
     validate,
     grain,

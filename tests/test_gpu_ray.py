@@ -85,7 +85,7 @@ def test_ray_rejects_bad_arguments(E, scene):
     import torch
     s = torch.from_numpy(scene["scene"]).cuda()
     out = torch.zeros((64 * 64, 4), device="cuda")
-    for ns, nl, Wd, depth, lws in [(300, 3, 64, 3, 128), (64, 20, 64, 3, 128), (64, 3, 0, 3, 128),
+    for ns, nl, Wd, depth, lws in [(129, 3, 64, 3, 128), (64, 20, 64, 3, 128), (64, 3, 0, 3, 128),
                                    (64, 3, 64, -1, 128), (64, 3, 64, 3, 2048)]:
         eng = E.Engine(0)
         p = E.Program("ray").in_(s).out(out).args(s, ns, nl, Wd, 64, 0.1, 0.0, 0.0, 0.0, depth, out)
