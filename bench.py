@@ -190,6 +190,7 @@ class NBody(Workload):
     NFD = 256
 
     def host_setup(self):
+        self.sms = self.torch.cuda.get_device_properties(0).multi_processor_count if self.torch else 0
         self.n = 16384 if SMALL else 65536
         self.pos, _ = W.nbody_bodies(self.n)
         self.lws = 64
@@ -224,8 +225,11 @@ class NBody(Workload):
             (E.Program("nbody_acc").in_(pos).out(acc).args(pos, n, self.EPS2, acc), n, 64),
             (E.Program("nbody_energy").in_(pos).out(en).args(pos, n, self.EPS2, en), n, 64),
             (E.Program("nbody_adjoint").in_(pos).in_(gE).out(grad).args(pos, n, self.EPS2, gE, grad), n, 64),
+            # 256 samples of one CTA each: one device per SM, so no SM holds two samples
+            # while another holds none
             (E.Program("nbody_fd").in_(pos).in_(fb).in_(fc).out(fd)
-             .args(pos, n, self.EPS2, 1e-3, fb, fc, self.NFD, fd), self.NFD, 1),
+             .args(pos, n, self.EPS2, 1e-3, fb, fc, self.NFD, fd), self.NFD, 1,
+             (0 if D == 0 and C == 0 else self.sms, 0 if D == 0 and C == 0 else 1)),
         ]
         return MultiEngine(E, progs, sched, params, D, C)
 
@@ -444,11 +448,13 @@ class MultiEngine:
 
     def __init__(self, E, progs, sched, params, D, C):
         self.engs = []
-        self.names = [pr.kernel for pr, _, _ in progs]
-        self.wis = [g for _, g, _ in progs]
-        for prog, gws, lws in progs:
+        self.names = [pr[0].kernel for pr in progs]
+        self.wis = [pr[1] for pr in progs]
+        for pr in progs:
+            prog, gws, lws = pr[:3]
+            d, c = pr[3] if len(pr) > 3 else (D, C)  # a program may name its own workers
             e = E.Engine(0)
-            e.work_items(gws, lws).scheduler(sched, params).workers(D if lws > 1 else 0, C if lws > 1 else 0)
+            e.work_items(gws, lws).scheduler(sched, params).workers(d, c)
             e.program(prog)
             self.engs.append(e)
 
