@@ -144,29 +144,38 @@ struct Opt {
     bool put;
 };
 
-enum LeafKind { LEAF_PRICE = 0, LEAF_DELTA = 1, LEAF_VEGA = 2 };
-
-// One backward induction from the leaves of `kind` (only in-the-money leaves
-// of the priced side are non-zero).  Returns the root on lane 0 (scaled by
-// 2^shift); for the price leaves d1 receives B_1 - B_0.
-__device__ __forceinline__ float lattice(const Opt &o, int kind, float *sh, int lane, int &shift, float &d1)
+// The leaves 0..N of the priced side (zero where out of the money and
+// beyond N) into shared buffer 0 (price), and with greeks also into buffers
+// 1 (delta: dS_T/dS) and 2 (vega leaf part: dS_T/dsigma), one exp per leaf.
+__device__ __forceinline__ void leaves(const Opt &o, float *sh, int lane, bool greeks)
 {
     __syncwarp();
     for (int j = lane; j <= kMaxSteps; j += kWarp) {
-        float v = 0.f;
+        float b = 0.f, dl = 0.f, vg = 0.f;
         if (j <= o.N) {
             const float m = (float)(2 * j - o.N);
             const float g = expf(o.a * m);
             const float ST = o.S * g;
             if (o.put ? (ST < o.K) : (ST > o.K)) {
-                if (kind == LEAF_PRICE) v = o.put ? o.K - ST : ST - o.K;
-                else if (kind == LEAF_DELTA) v = o.put ? -g : g;
-                else v = o.put ? -(ST * m * o.sdt) : ST * m * o.sdt;
+                b = o.put ? o.K - ST : ST - o.K;
+                dl = o.put ? -g : g;
+                vg = o.put ? -(ST * m * o.sdt) : ST * m * o.sdt;
             }
         }
-        sh[shidx(j)] = v;
+        sh[shidx(j)] = b;
+        if (greeks) {
+            sh[kShNodes + shidx(j)] = dl;
+            sh[2 * kShNodes + shidx(j)] = vg;
+        }
     }
     __syncwarp();
+}
+
+// One backward induction from the leaves in `sh` (which it then uses as the
+// repack buffer).  Returns the root on lane 0 (scaled by 2^shift) and, on
+// lane 0, d1 = B_1 - B_0 of level 1 at the root's scaling.
+__device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, int &shift, float &d1)
+{
     Lat L;
     L.q2 = o.q2;
     L.active = o.N;  // nodes of level N-1
@@ -219,10 +228,11 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     int shift = 0;
     float d1 = 0.f, root[3] = {0.f, 0.f, 0.f};
     const int passes = (G && p.greeks) ? 3 : 1;
+    leaves(op, sh, lane, passes == 3);
 #pragma unroll 1
     for (int k = 0; k < passes; ++k) {
         float dk;
-        const float r = lattice(op, k, sh, lane, shift, dk);
+        const float r = lattice(op, sh + k * kShNodes, lane, shift, dk);
         if (k == 0) {
             root[0] = r;
             d1 = dk;
@@ -271,7 +281,7 @@ struct BinoBody {
 template <bool G>
 __global__ void __launch_bounds__(kWarp) k_binomial(BinoParams prm, SchedArgs s)
 {
-    __shared__ float sh[kShNodes];
+    __shared__ float sh[(G ? 3 : 1) * kShNodes];
     BinoBody<G> b;
     b.p = prm;
     b.sh = sh;
@@ -339,7 +349,7 @@ struct BinoBatchBody {
 template <bool G>
 __global__ void __launch_bounds__(kWarp) k_binomial_batch(BinoBatchParams prm, SchedArgs s)
 {
-    __shared__ float sh[kShNodes];
+    __shared__ float sh[(G ? 3 : 1) * kShNodes];
     BinoBatchBody<G> b;
     b.p = prm;
     b.sh = sh;
