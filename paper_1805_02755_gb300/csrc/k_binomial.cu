@@ -5,7 +5,8 @@
 // One warp (the work-group, lws 32) prices one option.  Level t of the
 // lattice holds nodes j = 0..t; node j lives in lane j / R, register slot
 // j % R, where the width R steps down 64, 56, 48, ..., 2, 1 as the lattice
-// shrinks.  A backward step needs node j+1: in the same lane except for the
+// shrinks; a lattice starts at the narrowest width that holds its leaves
+// (each width's code exists once and is entered by index).  A backward step needs node j+1: in the same lane except for the
 // last slot, which one shuffle per level brings from the next lane.  When
 // the live nodes fit in the next width the warp repacks its registers
 // through a padded shared buffer, so ~90% of the computed slots stay live.
@@ -83,8 +84,9 @@ constexpr int kShNodes = kMaxSteps + 1 + kMaxSteps / 32 + 32;  // leaves 0..N wi
 
 __device__ __forceinline__ int shidx(int j) { return j + (j >> 5); }  // avoids bank conflicts
 
+// One backward level on the first R slots of B.
 template <int R>
-__device__ __forceinline__ void level(float (&B)[R], Lat &L)
+__device__ __forceinline__ void level(float (&B)[kMaxR], Lat &L)
 {
     const float bn = __shfl_down_sync(kFull, B[0], 1);
 #pragma unroll
@@ -101,32 +103,31 @@ __device__ __forceinline__ void level(float (&B)[R], Lat &L)
     }
 }
 
-// The tree from width R to width R2 through the warp's shared buffer.
-template <int R, int R2>
-__device__ __forceinline__ void repack(const float (&x)[R], float (&y)[R2], float *sh, int lane)
+// B[0..R) <- shared nodes lane*R .. lane*R + R - 1 at width R = width_at(WI).
+template <int WI>
+__device__ __forceinline__ void load_width(float (&B)[kMaxR], const float *sh, int lane)
 {
-    __syncwarp();
+    constexpr int R = width_at(WI);
 #pragma unroll
-    for (int s = 0; s < R; ++s) sh[shidx(lane * R + s)] = x[s];
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < R2; ++s) y[s] = sh[shidx(lane * R2 + s)];
+    for (int s = 0; s < R; ++s) B[s] = sh[shidx(lane * R + s)];
 }
 
-// Levels at width width_at(WI) until the live nodes fit the next width, then
-// repack and continue; lane 0 slot 0 ends up holding the root, and lane 0's
-// d1 the level-1 difference B_1 - B_0 at the root's scaling.
+// Width width_at(WI): levels until the live nodes fit the next width, then
+// the repack through the warp's shared buffer.  At the last width (1) the
+// levels run down to the root, keeping lane 0's level-1 difference
+// d1 = B_1 - B_0 at the root's scaling.
 template <int WI>
-__device__ __forceinline__ void phase(float (&B)[width_at(WI)], Lat &L, float *sh, int lane, float &d1)
+__device__ __forceinline__ void width_step(float (&B)[kMaxR], Lat &L, float *sh, int lane, float &d1)
 {
     constexpr int R = width_at(WI);
     constexpr int R2 = width_at(WI + 1);
     if constexpr (R2 > 0) {
         while (L.active > kWarp * R2) level<R>(B, L);
-        float b2[R2];
-        repack<R, R2>(B, b2, sh, lane);
-        phase<WI + 1>(b2, L, sh, lane, d1);
-        B[0] = b2[0];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < R; ++s) sh[shidx(lane * R + s)] = B[s];
+        __syncwarp();
+        load_width<WI + 1>(B, sh, lane);
     } else {
         while (L.active > 2) level<1>(B, L);
         if (L.active == 2) {
@@ -135,6 +136,35 @@ __device__ __forceinline__ void phase(float (&B)[width_at(WI)], Lat &L, float *s
             if (L.rescale == 0) d1 *= 0x1p-32f;
         }
     }
+}
+
+// Runtime width index -> the width's code (each width's code exists once).
+template <int WI>
+__device__ __forceinline__ void width_step_at(int wi, float (&B)[kMaxR], Lat &L, float *sh, int lane, float &d1)
+{
+    if constexpr (WI < kNWidths) {
+        if (wi == WI) width_step<WI>(B, L, sh, lane, d1);
+        else width_step_at<WI + 1>(wi, B, L, sh, lane, d1);
+    }
+}
+
+template <int WI>
+__device__ __forceinline__ void load_width_at(int wi, float (&B)[kMaxR], const float *sh, int lane)
+{
+    if constexpr (WI < kNWidths) {
+        if (wi == WI) load_width<WI>(B, sh, lane);
+        else load_width_at<WI + 1>(wi, B, sh, lane);
+    }
+}
+
+// The narrowest width index whose 32 lanes hold n nodes.
+template <int WI>
+__device__ __forceinline__ int width_for(int n)
+{
+    if constexpr (WI + 1 < kNWidths) {
+        if (kWarp * width_at(WI + 1) >= n) return width_for<WI + 1>(n);
+    }
+    return WI;
 }
 
 // Per-option constants of the lattice.
@@ -178,19 +208,31 @@ __device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, int 
 {
     Lat L;
     L.q2 = o.q2;
-    L.active = o.N;  // nodes of level N-1
-    L.rescale = 1;   // that level is formed from the leaves below
     L.shift = o.N;
-    // level N-1 at width 64: node j from leaves j and j+1
     float B[kMaxR];
+    int wi;
+    if (o.N + 1 <= kMaxSteps) {
+        // the N + 1 leaves as level N, at the narrowest width that holds them
+        wi = width_for<0>(o.N + 1);
+        load_width_at<0>(wi, B, sh, lane);
+        L.active = o.N + 1;
+        L.rescale = 0;
+    } else {
+        // N = 2048: 2049 leaves do not fit 32 x 64 slots; level N-1 from the leaves
+        wi = 0;
 #pragma unroll
-    for (int s = 0; s < kMaxR; ++s) {
-        const int j = lane * kMaxR + s;
-        const float lb = sh[shidx(j + 1)], b = sh[shidx(j)];
-        if (s == 0) d1 = lb - b;  // the level-1 difference when N == 1
-        B[s] = fmaf(L.q2, lb - b, lb + b);
+        for (int s = 0; s < kMaxR; ++s) {
+            const int j = lane * kMaxR + s;
+            const float lb = sh[shidx(j + 1)], b = sh[shidx(j)];
+            B[s] = fmaf(L.q2, lb - b, lb + b);
+        }
+        L.active = o.N;
+        L.rescale = 1;
     }
-    phase<0>(B, L, sh, lane, d1);
+    for (;; ++wi) {
+        width_step_at<0>(wi, B, L, sh, lane, d1);
+        if (wi == kNWidths - 1) break;
+    }
     shift = L.shift;
     return B[0];
 }
