@@ -101,6 +101,10 @@ class Workload:
 
     in_step = True  # False: reported per kernel beside the step (not one of the five configurations)
 
+    def tunable(self, name):
+        """(fresh-program factory, gws, lws) of a program the autotuner may search, or None."""
+        return None
+
     def programs(self):
         """(name, engine, work-items) of every program the step runs."""
         if isinstance(self.eng, MultiEngine):
@@ -189,6 +193,13 @@ class Gaussian(Workload):
         return 2048 / self.H, time.perf_counter() - t, "2048 of %d rows" % self.H
 
 
+def _single_program_tunable(self, name):
+    return (lambda: self.program(self.d_in, self.d_out), self.gws, self.lws) if name == self.name else None
+
+
+Gaussian.tunable = _single_program_tunable
+
+
 class NBody(Workload):
     """Config 3: force (HGuided), potential energy (FP64 sums), its adjoint and
     the finite-difference check, four launches over the same 65536 bodies."""
@@ -243,6 +254,12 @@ class NBody(Workload):
 
     def work_items(self):
         return 3 * self.n + self.NFD
+
+    def tunable(self, name):
+        if name != "nbody_acc":
+            return None
+        pos, acc = self.d_in[0], self.d_out[0]
+        return (lambda: self.E.Program("nbody_acc").in_(pos).out(acc).args(pos, self.n, self.EPS2, acc), self.n, 64)
 
     def alg(self, name):
         n = self.n
@@ -536,6 +553,8 @@ class Ray(Workload):
         return rows / self.Hd, time.perf_counter() - t, "%d of %d rows" % (rows, self.Hd)
 
 
+Ray.tunable = _single_program_tunable
+
 WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial, Gemm, Ray]
 
 
@@ -713,6 +732,8 @@ def run_ours(args):
             d[k2] = v2 / (ms * 1e-3)
         if hasattr(w, "batched_report") and not args.no_batched:
             d["batched"] = w.batched_report(timed)
+        if not args.no_autotune and w.tunable(name) is not None:
+            d["autotuned"] = autotune_report(w, name)
         if hasattr(w, "plain_engine"):  # the plain form beside the adjoint form
             pe = w.plain_engine()
             ms_plain = timed(pe.run, max(3, min(args.steps, 5)))
@@ -801,6 +822,23 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def autotune_report(w, name):
+    """The autotuner's search over devices, CTAs, HGuided k / minimum package and
+    Dynamic package counts for one program, next to the bench's own configuration
+    timed the same way (CUDA events, median of 3 after one warm-up run)."""
+    from paper_1805_02755_gb300 import autotune as AT
+    make, gws, lws = w.tunable(name)
+    s, p, D, C = w.sched
+    default = dict(scheduler=s, params=list(p), devices=D, ctas=C)
+    space = AT.default_space(name, gws // lws)
+    if default not in space:
+        space.append(default)
+    res = AT.autotune(name, make, gws, lws, space=space, reps=3, warmup=1, cache_path=None)
+    ms_default = next(ms for cfg, ms in res["table"] if cfg == default)
+    return dict(best=res["config"], ms_best=res["ms"], bench_config=default, ms_bench_config=ms_default,
+                candidates=len(res["table"]))
+
+
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
     """The largest value over the ranks (the slowest rank's time); every rank gets it."""
     if world <= 1:
@@ -882,6 +920,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="reduced sizes for profiler captures")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner's search for the tunable programs")
     args = ap.parse_args()
     global SMALL
     SMALL = args.small
