@@ -181,6 +181,22 @@ ecl_status ecl_worker_stats(ecl_engine *e, ecl_worker_stat *out, size_t cap, siz
  * turns it off.  The caller zeroes and owns the array. */
 ecl_status ecl_set_coverage(ecl_engine *e, uint32_t *counts, uint64_t n);
 
+/* Debug and fault-injection knobs (not in the paper; for tests of the
+ * failure path, which must not need a GPU fault).
+ *   ECL_DEBUG_SPIN_LIMIT  value = polls (about 128 ns apart) a CTA waiting
+ *                         for its device's next package makes before it
+ *                         gives up with ECL_ERR_TIMEOUT; 0 restores the
+ *                         default of 20,000,000.
+ *   ECL_DEBUG_WITHHOLD    value != 0: the CTA that fetches a device's next
+ *                         package (Dynamic / HGuided with more than one CTA
+ *                         per device) takes it but never publishes it, so
+ *                         the device's other CTAs wait out the spin limit:
+ *                         the run ends with ECL_ERR_TIMEOUT at the next
+ *                         synchronising call and the engine stays usable.
+ * Errors: ECL_ERR_ARG for an unknown kind or a negative value. */
+typedef enum { ECL_DEBUG_SPIN_LIMIT = 1, ECL_DEBUG_WITHHOLD = 2 } ecl_debug_kind;
+ecl_status ecl_debug(ecl_engine *e, int kind, int64_t value);
+
 /* Plan facts of the last run: G, the number of packages, D, C and the
  * number of CTAs launched.  Any pointer may be NULL. */
 ecl_status ecl_plan_info(const ecl_engine *e, uint64_t *G, uint64_t *packages,

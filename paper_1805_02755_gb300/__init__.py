@@ -30,6 +30,7 @@ ECL_STATIC, ECL_STATIC_REV, ECL_DYNAMIC, ECL_HGUIDED, ECL_MONOLITHIC = range(5)
 SCHEDULERS = {"static": ECL_STATIC, "static_rev": ECL_STATIC_REV, "dynamic": ECL_DYNAMIC,
               "hguided": ECL_HGUIDED, "monolithic": ECL_MONOLITHIC}
 ECL_ARG_BUF_IN, ECL_ARG_BUF_OUT, ECL_ARG_BUF_OUT_OPT, ECL_ARG_I32, ECL_ARG_I64, ECL_ARG_F32 = range(6)
+ECL_DEBUG_SPIN_LIMIT, ECL_DEBUG_WITHHOLD = 1, 2
 
 PKG_STAT_DTYPE = np.dtype([("off_wg", "<u8"), ("len_wg", "<u8"), ("t0_ns", "<u8"), ("t1_ns", "<u8"),
                            ("pkg", "<u4"), ("device", "<u4"), ("cta", "<u4"), ("smid", "<u4")])
@@ -70,6 +71,7 @@ def lib():
             "ecl_stats": (_st, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
             "ecl_worker_stats": (_st, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
             "ecl_set_coverage": (_st, [_vp, _vp, ctypes.c_uint64]),
+            "ecl_debug": (_st, [_vp, ctypes.c_int, ctypes.c_int64]),
             "ecl_plan_info": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                     ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                     ctypes.POINTER(ctypes.c_uint32)]),
@@ -186,6 +188,30 @@ def ecl_set_coverage(e, counts) -> None:
         _check(lib().ecl_set_coverage(e, None, 0), e)
     else:
         _check(lib().ecl_set_coverage(e, _vp(counts.data_ptr()), counts.numel()), e)
+
+
+def ecl_debug(e, kind: int, value: int) -> None:
+    _check(lib().ecl_debug(e, int(kind), int(value)), e)
+
+
+def chrome_trace(stats: np.ndarray, path: Optional[str] = None, name: str = "ecl") -> dict:
+    """Per-package records (``ecl_stats``) as a Chrome trace (chrome://tracing,
+    Perfetto): one complete event per package, process = device, thread = the
+    CTA that fetched it, times in microseconds from the first fetch.  Written
+    to ``path`` when given; the trace dict is returned either way."""
+    events = []
+    t0 = int(stats["t0_ns"].min()) if len(stats) else 0
+    for r in stats:
+        events.append({"name": "pkg %d" % int(r["pkg"]), "cat": name, "ph": "X",
+                       "ts": (int(r["t0_ns"]) - t0) / 1e3, "dur": max(0, int(r["t1_ns"]) - int(r["t0_ns"])) / 1e3,
+                       "pid": int(r["device"]), "tid": int(r["cta"]),
+                       "args": {"off_wg": int(r["off_wg"]), "len_wg": int(r["len_wg"]), "smid": int(r["smid"])}})
+    trace = {"traceEvents": events, "displayTimeUnit": "ns"}
+    if path:
+        import json
+        with open(path, "w") as f:
+            json.dump(trace, f)
+    return trace
 
 
 def ecl_plan_info(e) -> dict:
@@ -452,6 +478,14 @@ class Engine:
     def set_coverage(self, counts):
         ecl_set_coverage(self.h, counts)
         return self
+
+    def debug(self, kind: int, value: int):
+        ecl_debug(self.h, kind, value)
+        return self
+
+    def trace(self, path: Optional[str] = None) -> dict:
+        """The last run's packages as a Chrome trace (see chrome_trace)."""
+        return chrome_trace(self.stats(), path)
 
     def last_error(self) -> str:
         return ecl_last_error(self.h)

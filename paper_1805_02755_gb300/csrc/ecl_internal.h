@@ -77,6 +77,7 @@ struct SchedArgs {
     uint32_t D, C;
     uint32_t mono_nchunks; // MODE_MONO: chunks of the whole range (= grid)
     uint32_t spin_limit;   // iterations of a bounded wait before giving up
+    uint32_t withhold;     // fault injection: fetchers do not publish packages
     // HGuided with unequal powers (MODE_HGUIDED)
     double hg_k;
     double hg_sum_p;

@@ -123,6 +123,8 @@ struct ecl_engine {
     std::vector<uint32_t> hg_uploaded_min;
     uint32_t *coverage = nullptr;
     uint64_t coverage_n = 0;
+    uint32_t spin_limit = 20000000u;  // ecl_debug knobs
+    uint32_t withhold = 0;
     Workspace ws;
     // facts of the last run
     uint64_t last_G = 0, last_npkg = 0;
@@ -455,6 +457,20 @@ ecl_status ecl_set_coverage(ecl_engine *e, uint32_t *counts, uint64_t n)
     return ECL_OK;
 }
 
+ecl_status ecl_debug(ecl_engine *e, int kind, int64_t value)
+{
+    if (!e) return ECL_ERR_ARG;
+    if (value < 0) return fail(e, ECL_ERR_ARG, "ecl_debug: negative value");
+    if (kind == ECL_DEBUG_SPIN_LIMIT) {
+        e->spin_limit = value == 0 ? 20000000u : (uint32_t)std::min<int64_t>(value, 0xffffffffll);
+    } else if (kind == ECL_DEBUG_WITHHOLD) {
+        e->withhold = value ? 1u : 0u;
+    } else {
+        return fail(e, ECL_ERR_ARG, "ecl_debug: unknown kind %d", kind);
+    }
+    return ECL_OK;
+}
+
 const char *ecl_last_error(const ecl_engine *e)
 {
     if (!e) return "NULL engine";
@@ -673,7 +689,8 @@ ecl_status ecl_run(ecl_engine *e)
     s.mode = pl.mode;
     s.D = D;
     s.C = C;
-    s.spin_limit = 20000000u;
+    s.spin_limit = e->spin_limit;
+    s.withhold = e->withhold;
     s.coverage = e->coverage;
     if (e->coverage && e->coverage_n < G)
         return fail(e, ECL_ERR_BUFFER, "coverage array has %llu entries, G = %llu",

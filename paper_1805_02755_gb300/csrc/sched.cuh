@@ -193,6 +193,10 @@ __device__ Claim claim_chunks(const SchedArgs &s, const typename Body::Params &b
         }
         if (t == nch) {  // this CTA fetches the device's next package
             const int64_t p = fetch_package<Body>(s, bp, d);
+            if (s.withhold) {  // fault injection: never publish; the others time out
+                c.done = 1;
+                return c;
+            }
             if (p < 0) {
                 atomicExch(&s.dev[d].word, (unsigned long long)kSlotDone << 32);
                 c.done = 1;

@@ -16,3 +16,27 @@ def test_split_uneven_sums_and_skews():
         assert sum(s) == n and len(s) == parts and min(s) >= 1
     s = np.array(split_uneven(1 << 20, 64, seed=1))
     assert s.max() > 8 * np.median(s)
+
+
+def test_chrome_trace_of_package_records(tmp_path):
+    import json
+    import numpy as np
+    import paper_1805_02755_gb300 as E
+    st = np.zeros(3, dtype=E.PKG_STAT_DTYPE)
+    st["t0_ns"] = [1000, 1500, 4000]
+    st["t1_ns"] = [3000, 5000, 4000]
+    st["pkg"] = [0, 1, 2]
+    st["device"] = [0, 1, 0]
+    st["cta"] = [3, 7, 3]
+    st["off_wg"] = [0, 4, 8]
+    st["len_wg"] = [4, 4, 2]
+    path = str(tmp_path / "t.json")
+    tr = E.chrome_trace(st, path)
+    ev = tr["traceEvents"]
+    assert [e["ph"] for e in ev] == ["X"] * 3
+    assert [e["ts"] for e in ev] == [0.0, 0.5, 3.0]  # microseconds from the first fetch
+    assert [e["dur"] for e in ev] == [2.0, 3.5, 0.0]
+    assert [(e["pid"], e["tid"]) for e in ev] == [(0, 3), (1, 7), (0, 3)]
+    assert ev[1]["args"] == {"off_wg": 4, "len_wg": 4, "smid": 0}
+    assert json.load(open(path)) == tr
+    assert E.chrome_trace(st[:0])["traceEvents"] == []
