@@ -460,6 +460,12 @@ class Engine:
 
     def run(self):
         ecl_run(self.h)
+        trace_dir = os.environ.get("ECL_TRACE")
+        if trace_dir:  # debugging aid: every run's packages as a Chrome trace (synchronises)
+            os.makedirs(trace_dir, exist_ok=True)
+            Engine._traces = getattr(Engine, "_traces", 0) + 1
+            kernel = self.program_obj.kernel if self.program_obj is not None else "run"
+            self.trace(os.path.join(trace_dir, "ecl_%s_%04d.json" % (kernel, Engine._traces)))
         return self
 
     def synchronize(self):
@@ -484,7 +490,8 @@ class Engine:
         return self
 
     def trace(self, path: Optional[str] = None) -> dict:
-        """The last run's packages as a Chrome trace (see chrome_trace)."""
+        """The last run's packages as a Chrome trace (see chrome_trace).  With the
+        environment variable ECL_TRACE set to a directory, every run writes one."""
         return chrome_trace(self.stats(), path)
 
     def last_error(self) -> str:

@@ -92,3 +92,20 @@ def test_debug_rejects_bad_knobs(E):
     with pytest.raises(E.EclError):
         eng.debug(E.ECL_DEBUG_SPIN_LIMIT, -1)
     eng.close()
+
+
+def test_trace_env_writes_chrome_traces(E, tmp_path, monkeypatch):
+    import json
+    import torch
+    monkeypatch.setenv("ECL_TRACE", str(tmp_path))
+    Wd, H = 128, 64
+    out = torch.zeros(Wd * H, dtype=torch.int32, device="cuda")
+    eng = E.Engine(0)
+    p = E.Program("mandelbrot").out(out).args(out, Wd, H, -2.0, -1.5, 3.0 / Wd, 3.0 / H, 32)
+    eng.work_items(Wd * H // 4, 256).scheduler("dynamic", (4,)).workers(2, 0).program(p)
+    eng.run()
+    files = sorted(tmp_path.glob("ecl_mandelbrot_*.json"))
+    assert len(files) == 1
+    ev = json.load(open(files[0]))["traceEvents"]
+    assert len(ev) == 4 and sum(e["args"]["len_wg"] for e in ev) == Wd * H // 4 // 256
+    eng.close()
