@@ -50,10 +50,7 @@ SMALL = False  # --small: reduced sizes for profiler captures (never a bench val
 EXTRA_PROGRAMS = {"gemm_split6"}
 
 # ncu-measured DRAM bytes per launch of the dominant kernel (null once the kernel changes)
-NCU_TRAFFIC = {
-    "binomial": {"bytes_per_launch": 1057.536e3 * 64,
-                 "source": "profiles/binomial_greeks_16384_options.md (16384 options x 64)"},
-}
+NCU_TRAFFIC = {}
 METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
 L2_FLUSH_BYTES = 512 << 20
 SMS_NOMINAL = 152
@@ -375,9 +372,10 @@ class Binomial(Workload):
                     batched_over_plain=ms_batched / ms_plain)
 
     def after(self):
-        # FP32 instructions per node update: three lattices (price, delta, vega leaf
-        # part) of 3 each (add, sub, FMA); flops with FMA = 2: 3 x 4
-        return dict(bound="alu", inst=9.0 * self.nodes, flops=12.0 * self.nodes, unit_name="options/s",
+        # FP32 instructions per node update: the price lattice and its adjoint
+        # (which gives delta and the vega leaf part) of 3 each (add, sub, FMA);
+        # flops with FMA = 2: 2 x 4
+        return dict(bound="alu", inst=6.0 * self.nodes, flops=8.0 * self.nodes, unit_name="options/s",
                     units=self.n, extra={"node_updates_per_s": self.nodes})
 
     def cpu_sample(self, O, threads):

@@ -82,79 +82,100 @@ constexpr int kMaxR = 64;
 constexpr int kMaxSteps = kWarp * kMaxR;               // deepest lattice: 2048 steps
 constexpr int kShNodes = kMaxSteps + 1 + kMaxSteps / 32 + 32;  // leaves 0..N with padding
 
+// Resident one-warp CTAs per SM the register budget is set for (255
+// registers a thread).  Measured on the 2^20-option batch with greeks:
+// 8 -> 193.5 ms; 12 (168 registers) 250 ms, 16 (128) 286 ms, 20 (96, with
+// spills) 309 ms: a tighter budget costs the level loops more than the extra
+// warps win back.
+constexpr int kMinCtas = 8;
+
 __device__ __forceinline__ int shidx(int j) { return j + (j >> 5); }  // avoids bank conflicts
 
-// One backward level on the first R slots of B.
+// One level of the recursion B'_k = (B_k + B_{k+1}) + 2q (B_{k+1} - B_k) on
+// the first R slots of every lane (lane l holds nodes l*R .. l*R + R - 1).
+// The last lane's last slot takes node 0 as its upper neighbour (`src` =
+// lane + 1 mod 32): a dead slot in the backward induction, and in the
+// adjoint (stored reversed) node 0 is still zero whenever that slot is read.
 template <int R>
-__device__ __forceinline__ void level(float (&B)[kMaxR], Lat &L)
+__device__ __forceinline__ void level(float (&B)[kMaxR], float q2, int src)
 {
-    const float bn = __shfl_down_sync(kFull, B[0], 1);
+    const float bn = __shfl_sync(kFull, B[0], src);
 #pragma unroll
     for (int s = 0; s < R; ++s) {
         const float up = (s + 1 < R) ? B[s + 1] : bn;
-        B[s] = fmaf(L.q2, up - B[s], up + B[s]);
-    }
-    L.active -= 1;
-    if (++L.rescale == 32) {
-        L.rescale = 0;
-        L.shift -= 32;
-#pragma unroll
-        for (int s = 0; s < R; ++s) B[s] *= 0x1p-32f;
+        B[s] = fmaf(q2, up - B[s], up + B[s]);
     }
 }
 
-// B[0..R) <- shared nodes lane*R .. lane*R + R - 1 at width R = width_at(WI).
+// B[0..R) <- shared nodes lane*R .. lane*R + R - 1 at width R = width_at(WI),
+// zero below node `lo`.
 template <int WI>
-__device__ __forceinline__ void load_width(float (&B)[kMaxR], const float *sh, int lane)
+__device__ __forceinline__ void load_width(float (&B)[kMaxR], const float *sh, int lane, int lo)
 {
     constexpr int R = width_at(WI);
 #pragma unroll
-    for (int s = 0; s < R; ++s) B[s] = sh[shidx(lane * R + s)];
+    for (int s = 0; s < R; ++s) {
+        const int j = lane * R + s;
+        B[s] = (j >= lo) ? sh[shidx(j)] : 0.f;
+    }
 }
 
-// Width width_at(WI): levels until the live nodes fit the next width, then
-// the repack through the warp's shared buffer.  At the last width (1) the
-// levels run down to the root, keeping lane 0's level-1 difference
-// d1 = B_1 - B_0 at the root's scaling.
+// `n` levels at width width_at(WI); then, unless soff < 0, every lane's R
+// slots to the warp's shared buffer at nodes soff + lane*R + s.
 template <int WI>
-__device__ __forceinline__ void width_step(float (&B)[kMaxR], Lat &L, float *sh, int lane, float &d1)
+__device__ __forceinline__ void levels(float (&B)[kMaxR], Lat &L, float *sh, int lane, int n, int soff)
 {
     constexpr int R = width_at(WI);
-    constexpr int R2 = width_at(WI + 1);
-    if constexpr (R2 > 0) {
-        while (L.active > kWarp * R2) level<R>(B, L);
-        __syncwarp();
+    const int src = (lane + 1) & (kWarp - 1);
+    // in runs up to the next rescale (every 32 levels, by 2^-32: exact)
+    while (n > 0) {
+        const int m = min(n, 32 - L.rescale);
+#pragma unroll 1
+        for (int i = 0; i < m; ++i) level<R>(B, L.q2, src);
+        n -= m;
+        L.rescale += m;
+        if (L.rescale == 32) {
+            L.rescale = 0;
+            L.shift -= 32;
 #pragma unroll
-        for (int s = 0; s < R; ++s) sh[shidx(lane * R + s)] = B[s];
-        __syncwarp();
-        load_width<WI + 1>(B, sh, lane);
-    } else {
-        while (L.active > 2) level<1>(B, L);
-        if (L.active == 2) {
-            d1 = __shfl_down_sync(kFull, B[0], 1) - B[0];
-            level<1>(B, L);
-            if (L.rescale == 0) d1 *= 0x1p-32f;
+            for (int s = 0; s < R; ++s) B[s] *= 0x1p-32f;
         }
     }
+    if (soff < 0) return;
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < R; ++s) sh[shidx(soff + lane * R + s)] = B[s];
+    __syncwarp();
 }
 
-// Runtime width index -> the width's code (each width's code exists once).
+// Runtime width index -> the width's code.  Both the backward induction and
+// its adjoint go through these, so each width's level code exists once
+// (the instruction footprint, not the arithmetic, limits the deep lattices).
 template <int WI>
-__device__ __forceinline__ void width_step_at(int wi, float (&B)[kMaxR], Lat &L, float *sh, int lane, float &d1)
+__device__ __forceinline__ void levels_at(int wi, float (&B)[kMaxR], Lat &L, float *sh, int lane, int n, int soff)
 {
     if constexpr (WI < kNWidths) {
-        if (wi == WI) width_step<WI>(B, L, sh, lane, d1);
-        else width_step_at<WI + 1>(wi, B, L, sh, lane, d1);
+        if (wi == WI) levels<WI>(B, L, sh, lane, n, soff);
+        else levels_at<WI + 1>(wi, B, L, sh, lane, n, soff);
     }
 }
 
 template <int WI>
-__device__ __forceinline__ void load_width_at(int wi, float (&B)[kMaxR], const float *sh, int lane)
+__device__ __forceinline__ void load_width_at(int wi, float (&B)[kMaxR], const float *sh, int lane, int lo)
 {
     if constexpr (WI < kNWidths) {
-        if (wi == WI) load_width<WI>(B, sh, lane);
-        else load_width_at<WI + 1>(wi, B, sh, lane);
+        if (wi == WI) load_width<WI>(B, sh, lane, lo);
+        else load_width_at<WI + 1>(wi, B, sh, lane, lo);
     }
+}
+
+template <int WI>
+__device__ __forceinline__ int width_rt(int wi)
+{
+    if constexpr (WI + 1 < kNWidths) {
+        if (wi != WI) return width_rt<WI + 1>(wi);
+    }
+    return width_at(WI);
 }
 
 // The narrowest width index whose 32 lanes hold n nodes.
@@ -174,67 +195,146 @@ struct Opt {
     bool put;
 };
 
-// The leaves 0..N of the priced side (zero where out of the money and
-// beyond N) into shared buffer 0 (price), and with greeks also into buffers
-// 1 (delta: dS_T/dS) and 2 (vega leaf part: dS_T/dsigma), one exp per leaf.
-__device__ __forceinline__ void leaves(const Opt &o, float *sh, int lane, bool greeks)
+// Leaf j (0..N) of the priced side: its payoff and, for the greeks, its
+// derivatives dS_T/dS (delta) and dS_T/dsigma (vega leaf part); all zero out
+// of the money.  One exp per leaf.
+__device__ __forceinline__ float leaf(const Opt &o, int j, float &dl, float &vg)
+{
+    const float m = (float)(2 * j - o.N);
+    const float g = expf(o.a * m);
+    const float ST = o.S * g;
+    float b = 0.f;
+    dl = vg = 0.f;
+    if (o.put ? (ST < o.K) : (ST > o.K)) {
+        b = o.put ? o.K - ST : ST - o.K;
+        dl = o.put ? -g : g;
+        vg = o.put ? -(ST * m * o.sdt) : ST * m * o.sdt;
+    }
+    return b;
+}
+
+// The payoffs of leaves 0..N into the warp's shared buffer, zero beyond N.
+__device__ __forceinline__ void leaves(const Opt &o, float *sh, int lane)
 {
     __syncwarp();
     for (int j = lane; j <= kMaxSteps; j += kWarp) {
-        float b = 0.f, dl = 0.f, vg = 0.f;
-        if (j <= o.N) {
-            const float m = (float)(2 * j - o.N);
-            const float g = expf(o.a * m);
-            const float ST = o.S * g;
-            if (o.put ? (ST < o.K) : (ST > o.K)) {
-                b = o.put ? o.K - ST : ST - o.K;
-                dl = o.put ? -g : g;
-                vg = o.put ? -(ST * m * o.sdt) : ST * m * o.sdt;
-            }
-        }
-        sh[shidx(j)] = b;
-        if (greeks) {
-            sh[kShNodes + shidx(j)] = dl;
-            sh[2 * kShNodes + shidx(j)] = vg;
-        }
+        float dl, vg;
+        sh[shidx(j)] = (j <= o.N) ? leaf(o, j, dl, vg) : 0.f;
     }
     __syncwarp();
 }
 
-// One backward induction from the leaves in `sh` (which it then uses as the
-// repack buffer).  Returns the root on lane 0 (scaled by 2^shift) and, on
-// lane 0, d1 = B_1 - B_0 of level 1 at the root's scaling.
-__device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, int &shift, float &d1)
+// The lattice passes of one option over the leaves in shared buffer 0,
+// which each pass then uses as its repack buffer.
+//
+// Pass 0, the backward induction: from the N + 1 leaves (level N) down to
+// the root.  The widths are walked downwards: at width R the levels run until
+// the live nodes fit the next width, then the nodes are repacked through the
+// shared buffer.  Gives the root on lane 0 (scaled by 2^shift) and, on lane
+// 0, d1 = B_1 - B_0 of level 1 at the root's scaling.
+//
+// Pass 1 (greeks), its adjoint: weights A on the nodes of level N - 1 with
+// root = sum_j A_j x_j for any level N - 1 of this recursion.  From the root
+// (A = 1) outwards A'_j = (A_j + A_{j-1}) + 2q (A_{j-1} - A_j), one node more
+// per level.  Stored reversed (node j at slot 32R - 1 - j) this is the
+// backward level itself, with the slots not reached yet at zero, so it runs
+// on the same code while the widths are walked upwards.  Leaves node j of
+// level N - 1 at shared node 32 Rf - 1 - j (Rf returned in `rf`), with the
+// power of two in A in shift_a: N - 1 levels here, and the one that pushes
+// the leaves back to level N - 1, applied by the caller, counted too.
+//
+// Both passes go through one call of levels_at and one of load_width_at, so
+// each width's code exists once in the kernel: the instruction footprint,
+// not the arithmetic, limits the deep lattices.
+__device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, bool adj, int &shift, float &d1,
+                                         int &shift_a, int &rf)
 {
     Lat L;
     L.q2 = o.q2;
-    L.shift = o.N;
     float B[kMaxR];
-    int wi;
-    if (o.N + 1 <= kMaxSteps) {
-        // the N + 1 leaves as level N, at the narrowest width that holds them
-        wi = width_for<0>(o.N + 1);
-        load_width_at<0>(wi, B, sh, lane);
-        L.active = o.N + 1;
+    float root = 0.f;
+#pragma unroll 1
+    for (int pass = 0; pass < (adj ? 2 : 1); ++pass) {
+        L.shift = o.N;
         L.rescale = 0;
-    } else {
-        // N = 2048: 2049 leaves do not fit 32 x 64 slots; level N-1 from the leaves
-        wi = 0;
+        int wi, active, lo = 0;
+        bool load = false, captured = false;
+        if (pass == 0) {
+            if (o.N + 1 <= kMaxSteps) {
+                // the N + 1 leaves as level N, at the narrowest width that holds them
+                wi = width_for<0>(o.N + 1);
+                load = true;
+                active = o.N + 1;
+            } else {
+                // N = 2048: 2049 leaves do not fit 32 x 64 slots; level N-1 from the leaves
+                wi = 0;
 #pragma unroll
-        for (int s = 0; s < kMaxR; ++s) {
-            const int j = lane * kMaxR + s;
-            const float lb = sh[shidx(j + 1)], b = sh[shidx(j)];
-            B[s] = fmaf(L.q2, lb - b, lb + b);
+                for (int s = 0; s < kMaxR; ++s) {
+                    const int j = lane * kMaxR + s;
+                    const float lb = sh[shidx(j + 1)], b = sh[shidx(j)];
+                    B[s] = fmaf(L.q2, lb - b, lb + b);
+                }
+                active = o.N;
+                L.rescale = 1;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < kMaxR; ++s) B[s] = 0.f;
+            if (lane == kWarp - 1) B[0] = 1.0f;
+            wi = kNWidths - 1;
+            active = 1;
         }
-        L.active = o.N;
-        L.rescale = 1;
+        for (;;) {
+            if (load) load_width_at<0>(wi, B, sh, lane, lo);
+            const int R = width_rt<0>(wi);
+            int n, soff = 0, next = wi;
+            bool fin = false;
+            if (pass == 0) {
+                if (wi + 1 < kNWidths) {
+                    n = active - kWarp * width_rt<0>(wi + 1);
+                    next = wi + 1;
+                    load = true;
+                    lo = 0;
+                } else if (!captured) {  // width 1: down to level 1
+                    n = active - 2;
+                    soff = -1;
+                    load = false;
+                } else {                 // the root
+                    n = 1;
+                    soff = -1;
+                    fin = true;
+                }
+            } else {
+                const int cap = min(kWarp * R, o.N);
+                n = cap - active;
+                if (cap == o.N) {
+                    fin = true;
+                } else {
+                    next = wi - 1;
+                    soff = kWarp * (width_rt<0>(next) - R);
+                    load = true;
+                    lo = soff;
+                }
+            }
+            levels_at<0>(wi, B, L, sh, lane, n, soff);
+            active += pass == 0 ? -n : n;
+            if (fin) break;
+            if (pass == 0 && wi + 1 == kNWidths) {
+                d1 = __shfl_down_sync(kFull, B[0], 1) - B[0];
+                captured = true;
+            }
+            wi = next;
+        }
+        if (pass == 0) {
+            if (L.rescale == 0) d1 *= 0x1p-32f;
+            shift = L.shift;
+            root = B[0];
+        } else {
+            shift_a = L.shift;
+            rf = width_rt<0>(wi);
+        }
     }
-    for (;; ++wi) {
-        width_step_at<0>(wi, B, L, sh, lane, d1);
-        if (wi == kNWidths - 1) break;
-    }
-    shift = L.shift;
-    return B[0];
+    return root;
 }
 
 template <bool G>
@@ -265,43 +365,52 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     op.q2 = 2.0f * q;
     op.N = N;
     op.put = S > K;  // price the out-of-the-money side, then parity
-    // price, then (greeks) delta and the vega leaf part; one copy of the
-    // unrolled level code serves the three passes
+    // price by backward induction; with greeks one adjoint pass gives delta
+    // and the vega leaf part as dot products of its weights with the leaves
+    const bool greeks = G && p.greeks;
     int shift = 0;
-    float d1 = 0.f, root[3] = {0.f, 0.f, 0.f};
-    const int passes = (G && p.greeks) ? 3 : 1;
-    leaves(op, sh, lane, passes == 3);
-#pragma unroll 1
-    for (int k = 0; k < passes; ++k) {
-        float dk;
-        const float r = lattice(op, sh + k * kShNodes, lane, shift, dk);
-        if (k == 0) {
-            root[0] = r;
-            d1 = dk;
-        } else if (k == 1) {
-            root[1] = r;
-        } else {
-            root[2] = r;
+    float d1 = 0.f;
+    int shift_a = 0, rf = 0;
+    leaves(op, sh, lane);
+    const float b = lattice(op, sh, lane, greeks, shift, d1, shift_a, rf);
+    float delta = 0.f, vega = 0.f;
+    if (greeks) {
+        const int top = kWarp * rf - 1;  // node j of level N - 1 at shared node top - j
+        // leaf derivatives pushed back one level (x'_j from x_j, x_{j+1}),
+        // dotted with A; the leaves are evaluated again here rather than kept
+        // in shared memory (two buffers would halve the resident warps)
+        float sd = 0.f, sv = 0.f;
+        for (int j = lane; j < N; j += kWarp) {
+            const float w = sh[shidx(top - j)];
+            float d0, v0, d1l, v1;
+            leaf(op, j, d0, v0);
+            leaf(op, j + 1, d1l, v1);
+            sd = fmaf(w, fmaf(op.q2, d1l - d0, d1l + d0), sd);
+            sv = fmaf(w, fmaf(op.q2, v1 - v0, v1 + v0), sv);
         }
-    }
-    const float b = root[0];
-    float delta = root[1], vega = root[2];
-    if (passes == 3) {
-        const float q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));  // 2 dq/dsigma
-        vega = fmaf((float)N * q2p, d1, vega);
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            sd += __shfl_xor_sync(kFull, sd, o2);
+            sv += __shfl_xor_sync(kFull, sv, o2);
+        }
+        delta = sd;
+        vega = sv;
     }
     if (lane == 0) {
-        // remove the remaining 2^shift (exact), then discount
+        // remove the remaining powers of two (exact), then discount
         const float disc = expf(-p.r * T);
         const float scale = ldexpf(disc, -shift);
         float price = b * scale;
-        delta *= scale;
-        if (op.put) {
-            price += S - K * disc;
-            delta += 1.0f;
-        }
+        if (op.put) price += S - K * disc;
         p.price[o] = price;
-        if (G && p.greeks) p.greeks[o] = make_float2(delta, vega * scale);
+        if (greeks) {
+            const float scale_a = ldexpf(disc, -shift_a);
+            const float q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));  // 2 dq/dsigma
+            delta *= scale_a;
+            if (op.put) delta += 1.0f;
+            vega = fmaf((float)N * q2p, d1 * scale, vega * scale_a);
+            p.greeks[o] = make_float2(delta, vega);
+        }
     }
 }
 
@@ -321,9 +430,9 @@ struct BinoBody {
 };
 
 template <bool G>
-__global__ void __launch_bounds__(kWarp) k_binomial(BinoParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kWarp, kMinCtas) k_binomial(BinoParams prm, SchedArgs s)
 {
-    __shared__ float sh[(G ? 3 : 1) * kShNodes];
+    __shared__ float sh[kShNodes];
     BinoBody<G> b;
     b.p = prm;
     b.sh = sh;
@@ -389,9 +498,9 @@ struct BinoBatchBody {
 };
 
 template <bool G>
-__global__ void __launch_bounds__(kWarp) k_binomial_batch(BinoBatchParams prm, SchedArgs s)
+__global__ void __launch_bounds__(kWarp, kMinCtas) k_binomial_batch(BinoBatchParams prm, SchedArgs s)
 {
-    __shared__ float sh[(G ? 3 : 1) * kShNodes];
+    __shared__ float sh[kShNodes];
     BinoBatchBody<G> b;
     b.p = prm;
     b.sh = sh;

@@ -288,15 +288,25 @@ template <class Body>
 __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
 {
     __shared__ Claim sc;
-    if (s.mode == MODE_MONO) {  // the whole range is one package, CTA b = chunk b
-        body.run(0, s.G, blockIdx.x, s.mono_nchunks);
-        return;
-    }
-    const uint32_t d = blockIdx.x / s.C;
+    // MODE_MONO: the whole range is one package, CTA b = chunk b.  It goes
+    // through the same call of body.run, so that a large body is inlined once.
+    const bool mono = s.mode == MODE_MONO;
+    const uint32_t d = mono ? 0u : blockIdx.x / s.C;
     uint64_t t_first = 0, t_last = 0, busy = 0;
     uint32_t nchunks_done = 0;
     for (;;) {
-        if (threadIdx.x == 0) sc = claim_chunks<Body>(s, body.p, d);
+        if (threadIdx.x == 0) {
+            if (mono) {
+                Claim m{};
+                m.len = s.G;
+                m.t_begin = blockIdx.x;
+                m.t_end = blockIdx.x + 1;
+                m.nchunks = s.mono_nchunks;
+                sc = m;
+            } else {
+                sc = claim_chunks<Body>(s, body.p, d);
+            }
+        }
         __syncthreads();
         const Claim c = sc;
         __syncthreads();
@@ -304,6 +314,7 @@ __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
         uint64_t ts = 0;
         if (threadIdx.x == 0) ts = gtime();
         for (uint32_t t = c.t_begin; t < c.t_end; ++t) body.run(c.off, c.len, t, c.nchunks);
+        if (mono) return;
         __syncthreads();
         if (threadIdx.x == 0) {
             const uint64_t te = gtime();
