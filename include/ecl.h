@@ -54,7 +54,12 @@ typedef enum ecl_status {
 /* Schedulers of Sec. 5.3 and Sec. 7.3, plus the plain-grid baseline.
  *  ECL_STATIC      params: D-1 (or D) proportions; device d < D-1 gets
  *                  floor(prop_d * U) units, the last device the rest; no
- *                  params = equal split.  One package per device.
+ *                  params = equal split.  One package per device.  With
+ *                  D = 1 the single package [0, G) runs as one grid, one
+ *                  CTA per chunk (nothing is left to schedule at run time;
+ *                  the kernels with their own claim loop, the GEMMs, keep
+ *                  the queue); its package record has t0 = chunk 0's start,
+ *                  and there is one worker record per CTA.
  *  ECL_STATIC_REV  same sizes, ranges laid out in reverse device order
  *                  (Sec. 7.3 "Static rev").
  *  ECL_DYNAMIC     params: {num_packages}; equal packages of
@@ -92,7 +97,8 @@ typedef struct ecl_pkg_stat {
     uint32_t smid;    /* SM of that CTA */
 } ecl_pkg_stat;
 
-/* One record per persistent CTA. */
+/* One record per persistent CTA (per CTA of the grid when Static runs over
+ * one device). */
 typedef struct ecl_worker_stat {
     uint64_t t_first_ns; /* start of its first chunk (0 if it got none) */
     uint64_t t_last_ns;  /* end of its last chunk */
@@ -153,7 +159,8 @@ ecl_status ecl_workers(ecl_engine *e, int devices, int ctas_per_device);
 ecl_status ecl_engine_program(ecl_engine *e, ecl_program *p);
 
 /* Executes the whole NDRange once: validates, plans the packages,
- * then makes ONE persistent launch on the engine's stream.  With device
+ * then makes ONE launch on the engine's stream (persistent CTAs pulling
+ * packages; a plain grid for Static over one device).  With device
  * buffers only, it returns without waiting (use ecl_synchronize).  If the
  * program registered host buffers, inputs are copied to device mirrors
  * before the launch and outputs copied back after it, and the call waits

@@ -78,6 +78,8 @@ struct SchedArgs {
     uint32_t mono_nchunks; // MODE_MONO: chunks of the whole range (= grid)
     uint32_t spin_limit;   // iterations of a bounded wait before giving up
     uint32_t withhold;     // fault injection: fetchers do not publish packages
+    uint32_t records;      // MODE_MONO run for Static over one device: keep the
+                           // package record (table entry 0) and one worker record per CTA
     // HGuided with unequal powers (MODE_HGUIDED)
     double hg_k;
     double hg_sum_p;
@@ -139,6 +141,9 @@ struct KernelDesc {
     int (*ctas_per_sm)();
     // Launches the persistent (or monolithic) kernel.
     ecl_status (*launch)(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err);
+    // The kernel runs its own claim loop instead of drive/drive_ws (the
+    // tcgen05 GEMMs): Static over one device then stays on the queue.
+    bool own_claims;
 };
 
 const KernelDesc *find_kernel(const char *name);

@@ -547,13 +547,13 @@ ecl_status l_cast(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
 extern const KernelDesc kGemmBF16 = {
     "gemm_bf16", 6,
     {{"A", A_BUF_IN}, {"Bt", A_BUF_IN}, {"C", A_BUF_OUT}, {"M", A_I32}, {"N", A_I32}, {"K", A_I32}},
-    1, 1, NTHREADS, 4, v_bf16, grain_rows, nchunks_tiles, gemm_ctas_per_sm, l_bf16,
+    1, 1, NTHREADS, 4, v_bf16, grain_rows, nchunks_tiles, gemm_ctas_per_sm, l_bf16, true,
 };
 
 extern const KernelDesc kGemmSplit3 = {
     "gemm_split3", 6,
     {{"A", A_BUF_IN}, {"Bt", A_BUF_IN}, {"C", A_BUF_OUT}, {"M", A_I32}, {"N", A_I32}, {"K", A_I32}},
-    1, 1, NTHREADS, 4, v_split, grain_rows, nchunks_tiles, gemm_ctas_per_sm, l_split,
+    1, 1, NTHREADS, 4, v_split, grain_rows, nchunks_tiles, gemm_ctas_per_sm, l_split, true,
 };
 
 extern const KernelDesc kCastBF16 = {

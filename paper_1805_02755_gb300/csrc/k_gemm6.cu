@@ -497,7 +497,7 @@ extern const KernelDesc kGemmSplit6 = {
     "gemm_split6", 7,
     {{"A", A_BUF_IN}, {"Bt", A_BUF_IN}, {"C", A_BUF_OUT}, {"M", A_I32}, {"N", A_I32}, {"K", A_I32},
      {"chunk_k", A_I32}},
-    1, 1, NTHREADS, 4, validate, grain_rows, nchunks_tiles, ctas_per_sm, launch,
+    1, 1, NTHREADS, 4, validate, grain_rows, nchunks_tiles, ctas_per_sm, launch, true,
 };
 
 }  // namespace ecl

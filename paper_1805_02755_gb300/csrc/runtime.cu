@@ -696,6 +696,7 @@ ecl_status ecl_run(ecl_engine *e)
         return fail(e, ECL_ERR_BUFFER, "coverage array has %llu entries, G = %llu",
                     (unsigned long long)e->coverage_n, (unsigned long long)G);
     uint32_t grid;
+    bool grid_static = false;
     if (pl.mode == MODE_MONO) {
         const uint64_t nch = k->nchunks(a, e->gws, e->lws, 0, G);
         if (nch == 0 || nch > 0x7fffffffull)
@@ -712,6 +713,14 @@ ecl_status ecl_run(ecl_engine *e)
                                                  (unsigned long long)nch);
             pk.nchunks = (uint32_t)nch;
         }
+        // Static over one device leaves nothing to decide at run time: the
+        // device's single package [0, G) runs as one grid, CTA b = chunk b
+        // (as the paper's runtime enqueues one kernel per device package),
+        // with its package and worker records kept.  Kernels with their own
+        // claim loop stay on the queue.
+        grid_static = pl.mode == MODE_STATIC && D == 1 && pl.table.size() == 1 && !k->own_claims &&
+                      pl.table[0].off == 0 && pl.table[0].len == G && pl.table[0].nchunks > 0;
+        if (grid_static) grid = pl.table[0].nchunks;
         const size_t cap_need = pl.mode == MODE_HGUIDED ? (size_t)std::max<uint64_t>(pl.units, 1)
                                                         : std::max<size_t>(pl.table.size(), 1);
         if (cap_need > 0xffffffffull) return fail(e, ECL_ERR_SIZE, "too many packages");
@@ -790,6 +799,12 @@ ecl_status ecl_run(ecl_engine *e)
         s.npkg = (uint32_t)pl.table.size();
         s.dev = e->dev;
         s.wst = e->wst;
+        if (grid_static) {
+            s.mode = MODE_MONO;
+            s.records = 1;
+            s.mono_nchunks = grid;
+            C = grid;
+        }
     }
     s.q = e->q;
 

@@ -280,6 +280,65 @@ __device__ __forceinline__ void exit_protocol(const SchedArgs &s, uint32_t d, ui
     }
 }
 
+// Barrier among the compute warps only (warp-specialised driver).
+__device__ __forceinline__ void body_sync(uint32_t nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Records of a monolithic run of Static over one device (s.records): CTA b
+// ran chunk b of the single package, table entry 0.  The package's t0 is
+// chunk 0's start and t1 the running maximum of chunk end times (as in the
+// persistent Static path); every CTA writes its worker record.  With
+// coverage the last CTA to finish (a ticket on the queue's exit counter,
+// zero at the start of every run) counts the package's work-groups.  Called
+// by all NT threads that ran the body; WS selects the compute-warp barrier
+// of the warp-specialised driver.
+template <bool WS>
+__device__ __forceinline__ void grid_records(const SchedArgs &s, uint64_t ts, uint32_t *flag, uint32_t nt)
+{
+    if (WS) body_sync(nt);
+    else __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t te = gtime();
+        ecl_worker_stat w;
+        w.t_first_ns = ts;
+        w.t_last_ns = te;
+        w.busy_ns = te - ts;
+        w.cta = blockIdx.x;
+        w.device = 0;
+        w.smid = smid();
+        w.chunks = 1;
+        s.wst[blockIdx.x] = w;
+        PkgRec *r = s.rec;
+        if (blockIdx.x == 0) {
+            r->off = 0;
+            r->len = s.G;
+            r->t0 = ts;
+            r->pkg = 0;
+            r->device = 0;
+            r->cta = 0;
+            r->smid = w.smid;
+            r->nchunks = s.mono_nchunks;
+        }
+        atomicMax((unsigned long long *)&r->t1, (unsigned long long)te);
+        *flag = 0;
+        if (s.coverage) {
+            __threadfence();
+            if (atomicAdd(&s.q->exit_count, 1u) == gridDim.x - 1) {
+                s.q->exit_count = 0u;
+                *flag = 1;
+            }
+        }
+    }
+    if (s.coverage) {
+        if (WS) body_sync(nt);
+        else __syncthreads();
+        if (*flag)
+            for (uint64_t w = threadIdx.x; w < s.G; w += nt) atomicAdd(&s.coverage[w], 1u);
+    }
+}
+
 // The persistent driver.  Body must provide
 //   struct Params;                                   (kernel arguments)
 //   static __host__ __device__ uint32_t nchunks(const Params&, off, len);
@@ -314,7 +373,10 @@ __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
         uint64_t ts = 0;
         if (threadIdx.x == 0) ts = gtime();
         for (uint32_t t = c.t_begin; t < c.t_end; ++t) body.run(c.off, c.len, t, c.nchunks);
-        if (mono) return;
+        if (mono) {
+            if (s.records) grid_records<false>(s, ts, &sc.last, blockDim.x);
+            return;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             const uint64_t te = gtime();
@@ -382,12 +444,6 @@ __device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsign
     }
 }
 
-// Barrier among the compute warps only (warp-specialised driver).
-__device__ __forceinline__ void body_sync(uint32_t nthreads)
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-
 // Warp-specialised persistent driver: the CTA has Body::kThreads compute
 // threads plus one scheduler warp.  The scheduler warp claims chunks into a
 // two-slot ring ahead of the compute warps, so the atomic round trips of a
@@ -403,7 +459,12 @@ __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
     __shared__ uint64_t full[2], empty[2];
     __shared__ uint32_t flag;
     if (s.mode == MODE_MONO) {  // the whole range is one package, CTA b = chunk b
-        if (threadIdx.x < NC) body.run(0, s.G, blockIdx.x, s.mono_nchunks);
+        if (threadIdx.x < NC) {
+            uint64_t ts = 0;
+            if (s.records && threadIdx.x == 0) ts = gtime();
+            body.run(0, s.G, blockIdx.x, s.mono_nchunks);
+            if (s.records) grid_records<true>(s, ts, &flag, NC);
+        }
         return;
     }
     unsigned int *gerr = &s.q->error;
@@ -428,11 +489,25 @@ __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
     __syncthreads();
     if (threadIdx.x >= NC) {
         if (threadIdx.x == NC) {  // scheduler: lane 0 of the last warp
+            // Claiming a chunk ahead fixes which CTA takes it before anyone
+            // knows which CTA will be free first.  Under Static (direct
+            // claims on the device's chunk counter), when fewer chunks are
+            // left in the device's package than it has CTAs, the scheduler
+            // claims only after the chunk it handed out last is done (lazy),
+            // so the package's tail goes to the CTAs that finish first.
+            const bool counted = s.mode == MODE_STATIC && s.C > 1 && !s.coverage;
+            uint32_t nch = 0;
             for (uint32_t i = 0;; ++i) {
                 const uint32_t r = i & 1;
+                if (counted && i > 0) {
+                    const unsigned long long claimed = ld_relaxed(&s.dev[d].word);
+                    const bool lazy = claimed >= nch || nch - claimed < s.C;
+                    if (lazy && !sbar_wait(&empty[r ^ 1], ((i - 1) >> 1) & 1, gerr, 256)) break;
+                }
                 if (!sbar_wait(&empty[r], ((i >> 1) & 1) ^ 1, gerr, 4096)) break;
                 Claim c = (*(volatile unsigned int *)gerr) ? Claim{} : claim_chunks<Body>(s, body.p, d);
                 if (*(volatile unsigned int *)gerr) c.done = 1;
+                nch = c.nchunks;
                 ring[r] = c;
                 sbar_arrive(&full[r]);
                 if (c.done) break;

@@ -75,6 +75,44 @@ def test_config1_full_static_one_package(E, torch, oracle_mod):
     eng.close()
 
 
+def test_static_one_device_runs_as_one_grid(E, torch, oracle_mod):
+    """Static over one device has a single package [0, G) and nothing left to
+    decide at run time: it runs as one grid, CTA b = chunk b, keeping the
+    package record and one worker record per CTA.  Alternating with queue
+    runs on the same engine keeps every run exact and covered once."""
+    Wd, H, it = 1000, 37, 200
+    r = dict(x0=-2.0, y0=-1.5, dx=3.0 / Wd, dy=3.0 / H)
+    ref = oracle_img(oracle_mod, Wd, H, it, r)
+    lws = 64
+    gws = gws_for(Wd * H, lws)
+    G = gws // lws
+    out = torch.zeros(Wd * H + 4, dtype=torch.int32, device="cuda")
+    cov = torch.zeros(G, dtype=torch.int32, device="cuda")
+    eng = E.Engine(0)
+    eng.program(mandel_program(E, out, Wd, H, r["x0"], r["y0"], r["dx"], r["dy"], it)).set_coverage(cov)
+    for sched, params, D, C in (("static", (), 1, 0), ("dynamic", (7,), 3, 1), ("static", (), 1, 0),
+                                ("static_rev", (), 1, 5), ("hguided", (2.0, 1.0), 2, 3), ("static", (), 1, 0)):
+        out.zero_()
+        cov.zero_()
+        eng.work_items(gws, lws).scheduler(sched, params).workers(D, C)
+        eng.run()
+        eng.synchronize()
+        assert np.array_equal(out[: Wd * H].cpu().numpy().view(np.uint32).reshape(H, Wd), ref), sched
+        assert (cov.cpu().numpy() == 1).all(), sched
+        st, ws, info = eng.stats(), eng.worker_stats(), eng.plan_info()
+        if sched.startswith("static"):
+            assert info["devices"] == 1 and info["ctas"] == G and info["ctas_per_device"] == G
+            assert len(st) == 1 and int(st[0]["off_wg"]) == 0 and int(st[0]["len_wg"]) == G
+            assert len(ws) == G and (ws["chunks"] == 1).all() and (ws["device"] == 0).all()
+            assert sorted(ws["cta"].tolist()) == list(range(G))
+            assert (ws["t_last_ns"] >= ws["t_first_ns"]).all()
+            assert int(st[0]["t1_ns"]) == int(ws["t_last_ns"].max())
+            assert int(st[0]["t0_ns"]) == int(ws[ws["cta"] == 0]["t_first_ns"][0])
+        else:
+            assert int(ws["chunks"].sum()) >= len(st) >= 1
+    eng.close()
+
+
 SCHEDS = [
     ("static", (), 1, 0), ("static", (), 5, 1), ("static", (0.1, 0.2, 0.3), 4, 3),
     ("static_rev", (0.1, 0.2, 0.3), 4, 2), ("dynamic", (7,), 3, 1), ("dynamic", (50,), 2, 8),
