@@ -8,7 +8,8 @@ Configurations (seeded synthetic inputs, see workloads.py):
   binomial    2^20 options, depths U{256..2048}, price + delta + vega, HGuided
   gemm        8192^3, HGuided 128-row tiles: BF16 and split-BF16 three-product
 Beside the step (own per-kernel entries, not in the step's value): the
-six-product GEMM and the ray tracer (2048^2, 64 spheres).
+six-product GEMM, the ray tracer (2048^2, 64 spheres) and Mandelbrot scaled
+up to 8192^2 pixels and 1024 iterations.
 
 With N GPUs (torchrun) every rank runs the whole step on its own GPU
 (replicas); the step time is the slowest rank's and value counts all ranks.
@@ -133,7 +134,8 @@ class Mandelbrot(Workload):
         self.d_out = [torch.zeros(self.npx, dtype=torch.int32, device="cuda")]
         self.h_in = []
         self.h_out = [torch.zeros(self.npx, dtype=torch.int32).pin_memory()]
-        self.config = dict(size="1024x1024", max_iter=256, scheduler="static, 1 package")
+        self.config = dict(size="%dx%d" % (self.r["width"], self.r["height"]), max_iter=self.r["max_iter"],
+                           scheduler="static, 1 package")
 
     def program(self, ins, outs):
         r = self.r
@@ -556,7 +558,36 @@ class Ray(Workload):
 
 Ray.tunable = _single_program_tunable
 
-WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial, Gemm, Ray]
+
+class MandelbrotLarge(Mandelbrot):
+    """Config 1 scaled up, a secondary labelled row beside the step: 8192 x 8192
+    pixels over the same view, up to 1024 iterations, Static one package (the
+    1024 x 1024 case is too small to fill the GPU)."""
+    name = "mandelbrot_8192"
+    in_step = False
+
+    def host_setup(self):
+        n = 2048 if SMALL else 8192
+        self.r = W.mandelbrot_region(n, n, 1024)
+        self.npx = self.r["width"] * self.r["height"]
+        self.lws = 256
+        self.gws = self.npx // 4
+
+    def cpu_sample(self, O, threads):
+        # 64 evenly spaced rows, each through the oracle as a one-row image at
+        # that row's c_y (float32, as the kernel forms it)
+        r = self.r
+        rows = list(range(0, r["height"], r["height"] // 64))
+        t = time.perf_counter()
+        for j in rows:
+            cy = np.float32(r["y0"]) + np.float32(j) * np.float32(r["dy"])
+            O.mandelbrot(r["width"], 1, np.float32(r["x0"]), cy, np.float32(r["dx"]), np.float32(r["dy"]),
+                         r["max_iter"], threads=threads)
+        return len(rows) / r["height"], time.perf_counter() - t, "%d evenly spaced of %d rows" % (
+            len(rows), r["height"])
+
+
+WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial, Gemm, Ray, MandelbrotLarge]
 
 
 # ====================================================================== helpers
@@ -617,7 +648,11 @@ def balance_of(stats):
     return (min(f) / max(f)) if len(f) > 1 and max(f) > 0 else 1.0
 
 
-def worker_efficiency(ws):
+def worker_efficiency(ws, info):
+    """Mean over max busy time of the persistent CTAs; None for Static over one
+    device, which runs as a grid of one-chunk CTAs (no persistent workers)."""
+    if info["devices"] == 1 and info["ctas_per_device"] == info["ctas"] and len(ws) and (ws["chunks"] == 1).all():
+        return None
     busy = ws["busy_ns"].astype(np.float64)
     return float(busy.mean() / busy.max()) if len(busy) and busy.max() > 0 else None
 
@@ -693,8 +728,13 @@ def run_ours(args):
     step_ms = max_over_ranks(sum(tot) / len(tot), world)
     launches = sum(2 if name in ("gemm_split3", "gemm_split6") else 1 for _, name, _, _ in progs)  # split + main
 
+    def quantiles(ts):
+        q = sorted(ts)
+        at = lambda f: q[min(len(q) - 1, int(round(f * (len(q) - 1))))]  # noqa: E731
+        return dict(p10=at(0.1), median=statistics.median(q), p90=at(0.9), n=len(q))
+
     # scheduler overhead against the monolithic launch (same kernel body, no queue)
-    def timed(fn, n):
+    def timed(fn, n, samples=None):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         ts = []
@@ -705,6 +745,8 @@ def run_ours(args):
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
+        if samples is not None:
+            samples.extend(ts)
         return statistics.median(ts)
 
     kern = {}
@@ -716,8 +758,9 @@ def run_ours(args):
             monos[name] = eng
     for w, name, eng, wi in allprogs:
         extra = name in EXTRA_PROGRAMS or not w.in_step
-        ms_mono = timed(monos[name].run, max(5, min(args.steps, 10)))
-        ms_sched = timed(eng.run, max(5, min(args.steps, 10)))
+        mono_ts, sched_ts = [], []
+        ms_mono = timed(monos[name].run, max(5, min(args.steps, 10)), mono_ts)
+        ms_sched = timed(eng.run, max(5, min(args.steps, 10)), sched_ts)
         ms = ms_sched if extra else statistics.median(per[name])
         alg = w.alg(name)
         st = eng.stats()
@@ -726,8 +769,9 @@ def run_ours(args):
         d = dict(ms=ms, work_items=wi, work_items_per_s=wi / (ms * 1e-3),
                  overhead_vs_monolithic_pct=100.0 * (ms_sched - ms_mono) / ms_mono,
                  ms_monolithic=ms_mono, ms_scheduled_isolated=ms_sched, plan=info,
-                 balance_T_FD_over_T_LD=balance_of(st), cta_busy_efficiency=worker_efficiency(wst),
-                 packages=len(st))
+                 balance_T_FD_over_T_LD=balance_of(st), cta_busy_efficiency=worker_efficiency(wst, info),
+                 packages=len(st), ms_quantiles=quantiles(sched_ts if extra else per[name]),
+                 ms_monolithic_quantiles=quantiles(mono_ts))
         d[alg["unit_name"]] = alg["units"] / (ms * 1e-3)
         for k2, v2 in alg.get("extra", {}).items():
             d[k2] = v2 / (ms * 1e-3)
@@ -794,12 +838,15 @@ def run_ours(args):
     rf["traffic"] = None if (t is None or SMALL) else t["bytes_per_launch"]
     if t is not None and not SMALL:
         rf["traffic_source"] = t["source"]
+    probe = fp32_probe(E, torch, sms, clk.get("sm_mhz") or peaks["sm_max_mhz"])
     rf["peak_source"] = peaks["src"] if rf["bound"] not in ("alu", "mufu") else \
-        "derived: %d SMs x %d lanes x %.0f MHz (max SM clock); FP32 pipe measured 127 FMA/clk/SM" % (
-            sms, 128 if rf["bound"] == "alu" else 16, peaks["sm_max_mhz"])
+        "derived: %d SMs x %d lanes x %.0f MHz (max SM clock); the fp32_probe program measured %.1f FFMA/clk/SM " \
+        "at %.0f MHz in this run" % (sms, 128 if rf["bound"] == "alu" else 16, peaks["sm_max_mhz"],
+                                     probe["ffma_per_clk_per_sm"], probe["at_sm_mhz"])
     out = {
         "metric": METRIC, "value": value, "unit": "work-items/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": step_ms, "ms_per_step_quantiles": quantiles(tot),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, shaped like the paper's workloads)",
         "config": {"workload": "+".join(w.name for w in swls), "programs": {w.name: w.config for w in swls},
                    "beside_the_step": {w.name: w.config for w in wls if not w.in_step},
@@ -807,6 +854,7 @@ def run_ours(args):
         "e2e": {"value": job_rate(total_wi, world, e2e_s), "unit": "work-items/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
+        "fp32_probe": probe,
         "roofline": rf,
         "clocks": clk,
         "kernels": kern,
@@ -838,6 +886,35 @@ def autotune_report(w, name):
     ms_default = next(ms for cfg, ms in res["table"] if cfg == default)
     return dict(best=res["config"], ms_best=res["ms"], bench_config=default, ms_bench_config=ms_default,
                 candidates=len(res["table"]))
+
+
+def fp32_probe(E, torch, sms, sm_mhz, reps=10):
+    """FFMA throughput of the FP32 pipe, measured with the library's fp32_probe
+    program (independent FFMA chains, four waves of every CTA slot) through the
+    monolithic launch: the measured side of the FP32 rooflines."""
+    lws, iters = 256, 512
+    G = sms * 8 * 4
+    out = torch.empty(G * lws, device="cuda")
+    eng = E.Engine(0)
+    eng.work_items(G * lws, lws).scheduler("monolithic", ())
+    eng.program(E.Program("fp32_probe").out(out).args(out, iters, 0.999, 0.001))
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        eng.run()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        eng.run()
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    eng.close()
+    ms = statistics.median(ts)
+    rate = 128.0 * iters * G * lws / (ms * 1e-3)
+    return dict(ffma_per_s=rate, ms=ms, at_sm_mhz=sm_mhz, ffma_per_clk_per_sm=rate / (sms * sm_mhz * 1e6),
+                launch="%d CTAs x 256 threads, 8 chains x %d FFMA each" % (G, 16 * iters))
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:

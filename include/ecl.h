@@ -412,6 +412,12 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *
  * "cast_bf16"  (3 args, 1:1, any lws)  0 B in float[n]  1 B out bf16[n]
  *   2 S int64 n: round to nearest even (the input cast of "gemm_bf16").
+ *
+ * "fp32_probe"  (4 args, 1:1, lws 256)  0 B out float[gws]  1 S int32 iters
+ *   2 F32 m  3 F32 c: not a workload but the measured denominator of the
+ *   FP32 rooflines.  Work-item g runs 8 independent chains x <- fma(x, m, c)
+ *   of 16*iters steps and writes their sum: 128*iters FFMA per work-item
+ *   (m = 0.999, c = 0.001 keep the chains near 1).
  */
 
 #ifdef __cplusplus

@@ -33,6 +33,7 @@ SOURCES = {
     "k_gemm.cu": [],
     "k_gemm6.cu": [],
     "k_ray.cu": ["-fmad=false"],
+    "k_probe.cu": [],
 }
 HEADERS = ["ecl_internal.h", "sched.cuh", "f32x2.cuh", "tc.cuh"]
 

@@ -20,6 +20,7 @@ extern const KernelDesc kGemmSplit3;
 extern const KernelDesc kGemmSplit6;
 extern const KernelDesc kCastBF16;
 extern const KernelDesc kRay;
+extern const KernelDesc kFp32Probe;
 
 static const KernelDesc *const kAll[] = {
     &kMandelbrot,
@@ -36,6 +37,7 @@ static const KernelDesc *const kAll[] = {
     &kGemmSplit6,
     &kCastBF16,
     &kRay,
+    &kFp32Probe,
 };
 
 const KernelDesc *find_kernel(const char *name)

@@ -113,6 +113,29 @@ def test_static_one_device_runs_as_one_grid(E, torch, oracle_mod):
     eng.close()
 
 
+def test_scale_up_8192_sampled_rows_and_symmetry(E, torch, oracle_mod):
+    """The 8192^2, 1024-iteration scale-up (a row of the bench beside the step),
+    Static one package: sampled rows bit-exact against the oracle (each as a
+    one-row image at that row's c_y, formed in float32 as the kernel forms it),
+    and the whole image symmetric about y = 0: dy = 3 * 2^-13, so rows j and
+    8192 - j have c_y of opposite sign exactly, and the iteration commutes with
+    conjugation in IEEE arithmetic (negation is exact, rounding symmetric)."""
+    n, it = 8192, 1024
+    reg = W.mandelbrot_region(n, n, it)
+    r = dict(x0=reg["x0"], y0=reg["y0"], dx=reg["dx"], dy=reg["dy"])
+    eng, img, _, G, _ = run(E, torch, n, n, it, "static", (), D=1, region=r)
+    eng.close()
+    assert G == n * n // 4 // 256
+    assert np.array_equal(img[1:n // 2], img[n - 1:n // 2:-1])
+    rows = [0, 1, 2047, n // 2 - 1, n // 2, 5000, n - 1] + \
+        np.random.default_rng(1805).integers(0, n, 9).tolist()
+    for j in rows:
+        cy = np.float32(r["y0"]) + np.float32(j) * np.float32(r["dy"])
+        ref = oracle_mod.mandelbrot(n, 1, np.float32(r["x0"]), cy, np.float32(r["dx"]), np.float32(r["dy"]), it)
+        assert np.array_equal(img[j], ref[0]), j
+    assert int(img.max()) == it and int(img[0, 0]) == 1
+
+
 SCHEDS = [
     ("static", (), 1, 0), ("static", (), 5, 1), ("static", (0.1, 0.2, 0.3), 4, 3),
     ("static_rev", (0.1, 0.2, 0.3), 4, 2), ("dynamic", (7,), 3, 1), ("dynamic", (50,), 2, 8),
