@@ -130,25 +130,14 @@ struct ForceBody {
         }
     }
 
-    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    // Tiles [ta, tb) of the j-bodies for this thread's two bodies (X, Y, Z)
+    // and j-slice s of SPAN bodies per tile.  Tiles are double-buffered: the
+    // next tile's loads are in flight while the current one is computed, one
+    // barrier per tile.
+    template <uint32_t SPAN>
+    __device__ __forceinline__ void tiles(int64_t ta, int64_t tb, uint32_t s, f2 X, f2 Y, f2 Z, f2 EPS, f2 &AX,
+                                          f2 &AY, f2 &AZ, f2 &POT)
     {
-        const uint32_t half = p.lws / 2;
-        const uint32_t S = kFBlock / half;            // j-slices
-        const uint32_t b = threadIdx.x % half, s = threadIdx.x / half;
-        const uint64_t wg = off + t / p.seg;
-        const uint32_t sg = t % p.seg;
-        const int64_t i0 = (int64_t)wg * p.lws + b, i1 = i0 + half;
-        const bool v0 = i0 < p.n, v1 = i1 < p.n;
-        const float4 p0 = v0 ? __ldg(p.pos + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 p1 = v1 ? __ldg(p.pos + i1) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const f2 X = pk(p0.x, p1.x), Y = pk(p0.y, p1.y), Z = pk(p0.z, p1.z);
-        const f2 EPS = pk(p.eps2, p.eps2);
-        const uint32_t span = kFTile / S;
-        f2 AX = 0, AY = 0, AZ = 0, POT = 0;
-        const int64_t ntiles = (p.n + kFTile - 1) / kFTile;
-        const int64_t ta = ntiles * sg / p.seg, tb = ntiles * (sg + 1) / p.seg;
-        // tiles double-buffered: the next tile's loads are in flight while
-        // the current one is computed, one barrier per tile
         body_sync(kFBlock);  // the previous chunk is done with both buffers
         if (ta < tb) put_dup(shxy, shzm, tile_body(p.pos, p.n, ta));
         body_sync(kFBlock);
@@ -158,10 +147,10 @@ struct ForceBody {
             float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
             if (more) nxt = tile_body(p.pos, p.n, tile + 1);
             f2 TX = 0, TY = 0, TZ = 0, TP = 0;
-            const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + cur * kFTile + s * span);
-            const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + cur * kFTile + s * span);
-#pragma unroll 8
-            for (uint32_t k = 0; k < span; ++k) {
+            const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + cur * kFTile + s * SPAN);
+            const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + cur * kFTile + s * SPAN);
+#pragma unroll
+            for (uint32_t k = 0; k < SPAN; ++k) {
                 const ulonglong2 xy = qxy[k], zm = qzm[k];
                 const f2 dx = sub2(xy.x, X), dy = sub2(xy.y, Y), dz = sub2(zm.x, Z);
                 const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, EPS)));
@@ -182,6 +171,32 @@ struct ForceBody {
             // the other buffer was last read before the previous barrier
             if (more) put_dup(shxy + (cur ^ 1u) * kFTile, shzm + (cur ^ 1u) * kFTile, nxt);
             body_sync(kFBlock);
+        }
+    }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const uint32_t half = p.lws / 2;
+        const uint32_t S = kFBlock / half;            // j-slices
+        const uint32_t b = threadIdx.x % half, s = threadIdx.x / half;
+        const uint64_t wg = off + t / p.seg;
+        const uint32_t sg = t % p.seg;
+        const int64_t i0 = (int64_t)wg * p.lws + b, i1 = i0 + half;
+        const bool v0 = i0 < p.n, v1 = i1 < p.n;
+        const float4 p0 = v0 ? __ldg(p.pos + i0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 p1 = v1 ? __ldg(p.pos + i1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const f2 X = pk(p0.x, p1.x), Y = pk(p0.y, p1.y), Z = pk(p0.z, p1.z);
+        const f2 EPS = pk(p.eps2, p.eps2);
+        f2 AX = 0, AY = 0, AZ = 0, POT = 0;
+        const int64_t ntiles = (p.n + kFTile - 1) / kFTile;
+        const int64_t ta = ntiles * sg / p.seg, tb = ntiles * (sg + 1) / p.seg;
+        // the j-slice length kFTile / S equals half: one instance of the
+        // tile loop per lws, so that the pair loop's trip count is a constant
+        switch (half) {
+        case 16: tiles<16>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
+        case 32: tiles<32>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
+        case 64: tiles<64>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
+        default: tiles<128>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
         }
         // combine the slices of each body in slice order
         float ax0, ax1, ay0, ay1, az0, az1, pt0, pt1;
@@ -430,7 +445,9 @@ struct FDBody {
 };
 
 // ---------------------------------------------------------------- kernels
-template <uint32_t MODE>
+// One instance per launch form (FORM: DRIVE_MONO or DRIVE_QUEUE), each with
+// a single copy of the force body.
+template <uint32_t MODE, int FORM>
 __global__ void __launch_bounds__(kFBlock + 32, 3) k_nbody_force(NBodyParams prm, SchedArgs s)
 {
     extern __shared__ __align__(16) float4 fsm[];
@@ -441,7 +458,7 @@ __global__ void __launch_bounds__(kFBlock + 32, 3) k_nbody_force(NBodyParams prm
     b.shzm = fsm + 2 * kFTile;
     b.red = fsm;
     b.flag = &flag;
-    drive_ws(s, b);
+    drive_ws<ForceBody<MODE>, FORM>(s, b);
 }
 
 __global__ void __launch_bounds__(kBlock + 32) k_nbody_energy(EnergyParams prm, SchedArgs s)
@@ -480,8 +497,10 @@ int occ(const void *fn, int block = kBlock + 32, size_t smem = 0)
 template <uint32_t MODE>
 bool force_smem_ok()
 {
-    return cudaFuncSetAttribute((const void *)k_nbody_force<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kFSmem) == cudaSuccess;
+    return cudaFuncSetAttribute((const void *)k_nbody_force<MODE, DRIVE_QUEUE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem) == cudaSuccess &&
+           cudaFuncSetAttribute((const void *)k_nbody_force<MODE, DRIVE_MONO>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem) == cudaSuccess;
 }
 
 template <uint32_t MODE>
@@ -491,7 +510,7 @@ int occ_force()
         cudaGetLastError();
         return 0;
     }
-    return occ((const void *)k_nbody_force<MODE>, kFBlock + 32, kFSmem);
+    return occ((const void *)k_nbody_force<MODE, DRIVE_QUEUE>, kFBlock + 32, kFSmem);
 }
 
 template <uint32_t MODE>
@@ -502,7 +521,10 @@ ecl_status launch_force(const NBodyParams &p, const SchedArgs &s, const LaunchCt
         cudaGetLastError();
         return ECL_ERR_CUDA;
     }
-    k_nbody_force<MODE><<<c.grid, kFBlock + 32, kFSmem, c.stream>>>(p, s);
+    if (s.mode == MODE_MONO)
+        k_nbody_force<MODE, DRIVE_MONO><<<c.grid, kFBlock + 32, kFSmem, c.stream>>>(p, s);
+    else
+        k_nbody_force<MODE, DRIVE_QUEUE><<<c.grid, kFBlock + 32, kFSmem, c.stream>>>(p, s);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);
@@ -602,7 +624,7 @@ ecl_status l_step(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.out_pos = a.buf<float4>(5);
     p.out_vel = a.buf<float4>(6);
     p.lws = c.lws;
-    if (!force_ws(p, c, (const void *)k_nbody_force<NB_STEP>, err)) return ECL_ERR_CUDA;
+    if (!force_ws(p, c, (const void *)k_nbody_force<NB_STEP, DRIVE_QUEUE>, err)) return ECL_ERR_CUDA;
     return launch_force<NB_STEP>(p, s, c, err);
 }
 
@@ -628,7 +650,7 @@ ecl_status l_acc(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.eps2 = a.f32(2);
     p.out_acc = a.buf<float4>(3);
     p.lws = c.lws;
-    if (!force_ws(p, c, (const void *)k_nbody_force<NB_ACC>, err)) return ECL_ERR_CUDA;
+    if (!force_ws(p, c, (const void *)k_nbody_force<NB_ACC, DRIVE_QUEUE>, err)) return ECL_ERR_CUDA;
     return launch_force<NB_ACC>(p, s, c, err);
 }
 
@@ -659,7 +681,7 @@ ecl_status l_adj(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::st
     p.grad_E = a.buf<const float>(3);
     p.out_grad = a.buf<float4>(4);
     p.lws = c.lws;
-    if (!force_ws(p, c, (const void *)k_nbody_force<NB_ADJ>, err)) return ECL_ERR_CUDA;
+    if (!force_ws(p, c, (const void *)k_nbody_force<NB_ADJ, DRIVE_QUEUE>, err)) return ECL_ERR_CUDA;
     return launch_force<NB_ADJ>(p, s, c, err);
 }
 

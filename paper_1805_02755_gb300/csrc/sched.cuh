@@ -451,14 +451,23 @@ __device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsign
 // previous chunk's work.  Bodies synchronise with body_sync(kThreads), never
 // __syncthreads.  Every wait is bounded; a wait that gives up sets the queue's
 // error word and ends the CTA's work.
-template <class Body>
+// FORM selects the launch forms compiled into the kernel: DRIVE_ANY both
+// (chosen by s.mode at run time), DRIVE_MONO the monolithic launch only,
+// DRIVE_QUEUE the persistent queue only.  A kernel with a large body can be
+// instantiated once per form so that each holds a single inlined copy of the
+// body: with both copies in one function the force body's claim-loop copy
+// executed a third more instructions than its monolithic copy.
+enum DriveForm { DRIVE_ANY = 0, DRIVE_MONO = 1, DRIVE_QUEUE = 2 };
+
+template <class Body, int FORM = DRIVE_ANY>
 __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
 {
     constexpr uint32_t NC = Body::kThreads;
     __shared__ Claim ring[2];
     __shared__ uint64_t full[2], empty[2];
     __shared__ uint32_t flag;
-    if (s.mode == MODE_MONO) {  // the whole range is one package, CTA b = chunk b
+    if (FORM == DRIVE_MONO || (FORM == DRIVE_ANY && s.mode == MODE_MONO)) {
+        // the whole range is one package, CTA b = chunk b
         if (threadIdx.x < NC) {
             uint64_t ts = 0;
             if (s.records && threadIdx.x == 0) ts = gtime();
