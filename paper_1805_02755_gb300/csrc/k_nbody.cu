@@ -39,8 +39,13 @@ constexpr int kTile = 256;
 constexpr int kFBlock = 256;  // force CTA: 8 compute warps (+ the scheduler warp), 3 per SM
 constexpr int kFTile = 256;   // j-bodies per staged force tile
 // Force shared memory: two duplicated tiles (x,x,y,y) and (z,z,m,m), double
-// buffered; the slice partials reuse the first half after the tile loop.
-constexpr size_t kFSmem = 2 * 2 * kFTile * sizeof(float4);
+// buffered (the slice partials reuse the first half after the tile loop),
+// then each thread's running totals (a_x, a_y, a_z, potential) of its two
+// bodies, [4][kFBlock] packed pairs.  The totals change once per tile; kept
+// here rather than in registers they leave the pair loop its registers: with
+// them in registers, the claim-loop form of the kernel (72 registers at 3 CTAs
+// per SM) spent six register moves per pair iteration.
+constexpr size_t kFSmem = 2 * 2 * kFTile * sizeof(float4) + 4 * kFBlock * sizeof(unsigned long long);
 
 enum NMode : uint32_t { NB_STEP = 0, NB_ACC = 1, NB_ADJ = 2 };
 
@@ -104,6 +109,7 @@ struct ForceBody {
     Params p;
     float4 *shxy, *shzm;  // [2][kFTile] duplicated j-bodies, double-buffered
     float4 *red;          // [2 * kFBlock] slice partials (aliases shxy)
+    f2 *acc;              // [4][kFBlock] running totals of this thread's bodies
     uint32_t *flag;       // shared: this chunk completes its work-group
 
     static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t, uint64_t len)
@@ -135,9 +141,13 @@ struct ForceBody {
     // next tile's loads are in flight while the current one is computed, one
     // barrier per tile.
     template <uint32_t SPAN>
-    __device__ __forceinline__ void tiles(int64_t ta, int64_t tb, uint32_t s, f2 X, f2 Y, f2 Z, f2 EPS, f2 &AX,
-                                          f2 &AY, f2 &AZ, f2 &POT)
+    __device__ __forceinline__ void tiles(int64_t ta, int64_t tb, uint32_t s, f2 X, f2 Y, f2 Z, f2 EPS)
     {
+        f2 *A = acc + threadIdx.x;
+        A[0] = 0;
+        A[kFBlock] = 0;
+        A[2 * kFBlock] = 0;
+        if (MODE == NB_ADJ) A[3 * kFBlock] = 0;
         body_sync(kFBlock);  // the previous chunk is done with both buffers
         if (ta < tb) put_dup(shxy, shzm, tile_body(p.pos, p.n, ta));
         body_sync(kFBlock);
@@ -164,10 +174,10 @@ struct ForceBody {
                 TY = fma2(sc, dy, TY);
                 TZ = fma2(sc, dz, TZ);
             }
-            AX = add2(AX, TX);
-            AY = add2(AY, TY);
-            AZ = add2(AZ, TZ);
-            if (MODE == NB_ADJ) POT = add2(POT, TP);
+            A[0] = add2(A[0], TX);
+            A[kFBlock] = add2(A[kFBlock], TY);
+            A[2 * kFBlock] = add2(A[2 * kFBlock], TZ);
+            if (MODE == NB_ADJ) A[3 * kFBlock] = add2(A[3 * kFBlock], TP);
             // the other buffer was last read before the previous barrier
             if (more) put_dup(shxy + (cur ^ 1u) * kFTile, shzm + (cur ^ 1u) * kFTile, nxt);
             body_sync(kFBlock);
@@ -187,23 +197,23 @@ struct ForceBody {
         const float4 p1 = v1 ? __ldg(p.pos + i1) : make_float4(0.f, 0.f, 0.f, 0.f);
         const f2 X = pk(p0.x, p1.x), Y = pk(p0.y, p1.y), Z = pk(p0.z, p1.z);
         const f2 EPS = pk(p.eps2, p.eps2);
-        f2 AX = 0, AY = 0, AZ = 0, POT = 0;
         const int64_t ntiles = (p.n + kFTile - 1) / kFTile;
         const int64_t ta = ntiles * sg / p.seg, tb = ntiles * (sg + 1) / p.seg;
         // the j-slice length kFTile / S equals half: one instance of the
         // tile loop per lws, so that the pair loop's trip count is a constant
         switch (half) {
-        case 16: tiles<16>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
-        case 32: tiles<32>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
-        case 64: tiles<64>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
-        default: tiles<128>(ta, tb, s, X, Y, Z, EPS, AX, AY, AZ, POT); break;
+        case 16: tiles<16>(ta, tb, s, X, Y, Z, EPS); break;
+        case 32: tiles<32>(ta, tb, s, X, Y, Z, EPS); break;
+        case 64: tiles<64>(ta, tb, s, X, Y, Z, EPS); break;
+        default: tiles<128>(ta, tb, s, X, Y, Z, EPS); break;
         }
         // combine the slices of each body in slice order
-        float ax0, ax1, ay0, ay1, az0, az1, pt0, pt1;
-        upk(AX, ax0, ax1);
-        upk(AY, ay0, ay1);
-        upk(AZ, az0, az1);
-        upk(POT, pt0, pt1);
+        float ax0, ax1, ay0, ay1, az0, az1, pt0 = 0.f, pt1 = 0.f;
+        const f2 *A = acc + threadIdx.x;
+        upk(A[0], ax0, ax1);
+        upk(A[kFBlock], ay0, ay1);
+        upk(A[2 * kFBlock], az0, az1);
+        if (MODE == NB_ADJ) upk(A[3 * kFBlock], pt0, pt1);
         body_sync(kFBlock);
         red[threadIdx.x] = make_float4(ax0, ay0, az0, pt0);
         red[kFBlock + threadIdx.x] = make_float4(ax1, ay1, az1, pt1);
@@ -457,6 +467,7 @@ __global__ void __launch_bounds__(kFBlock + 32, 3) k_nbody_force(NBodyParams prm
     b.shxy = fsm;
     b.shzm = fsm + 2 * kFTile;
     b.red = fsm;
+    b.acc = reinterpret_cast<f2 *>(fsm + 4 * kFTile);
     b.flag = &flag;
     drive_ws<ForceBody<MODE>, FORM>(s, b);
 }

@@ -205,9 +205,13 @@ __device__ Claim claim_chunks(const SchedArgs &s, const typename Body::Params &b
             atomicExch(&s.dev[d].word, (unsigned long long)(p + 1) << 32);
             continue;
         }
-        // another CTA of the device is fetching: wait for the new slot
+        // another CTA of the device is fetching: wait for the new slot, with
+        // a doubling back-off (a fetch takes a few microseconds, and up to C - 1
+        // CTAs of the device poll meanwhile)
+        uint32_t ns = 128;
         while ((uint32_t)(ld_relaxed(&s.dev[d].word) >> 32) == slot) {
-            __nanosleep(128);
+            __nanosleep(ns);
+            if (ns < 2048) ns <<= 1;
             if (++spins > s.spin_limit) {
                 atomicExch(&s.q->error, (unsigned int)ECL_ERR_TIMEOUT);
                 atomicExch(&s.q->error_info, ((unsigned long long)blockIdx.x << 32) | spins);
@@ -422,7 +426,7 @@ __device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsign
                                           uint32_t max_sleep_ns)
 {
     uint64_t t0 = 0;
-    uint32_t ns = 32;
+    uint32_t ns = max_sleep_ns < 128 ? max_sleep_ns : 128;
     for (;;) {
         uint32_t ok;
         asm volatile(
