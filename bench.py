@@ -234,7 +234,8 @@ class NBody(Workload):
         self.h_out = [torch.zeros((n, 4)).pin_memory(), torch.zeros(1, dtype=torch.float64).pin_memory(),
                       torch.zeros((n, 4)).pin_memory(), torch.zeros(self.NFD, dtype=torch.float64).pin_memory()]
         self.config = dict(bodies=n, eps2=self.EPS2, lws=64, scheduler="hguided k=2 over 8 devices",
-                           programs="nbody_acc + nbody_energy + nbody_adjoint + nbody_fd(256 samples, h=1e-3)")
+                           programs="nbody_acc + nbody_energy + nbody_adjoint (HGuided) + nbody_fd (256 samples, "
+                                    "h=1e-3, Static one package)")
 
     def make_engine(self, sched, params, D=0, C=0, host=False):
         E = self.E
@@ -246,11 +247,10 @@ class NBody(Workload):
             (E.Program("nbody_acc").in_(pos).out(acc).args(pos, n, self.EPS2, acc), n, 64),
             (E.Program("nbody_energy").in_(pos).out(en).args(pos, n, self.EPS2, en), n, 64),
             (E.Program("nbody_adjoint").in_(pos).in_(gE).out(grad).args(pos, n, self.EPS2, gE, grad), n, 64),
-            # 256 samples of one CTA each: one device per SM, so no SM holds two samples
-            # while another holds none
+            # the finite-difference check (256 samples of one work-group each) is one
+            # Static package over one device: one grid, every sample resident at once
             (E.Program("nbody_fd").in_(pos).in_(fb).in_(fc).out(fd)
-             .args(pos, n, self.EPS2, 1e-3, fb, fc, self.NFD, fd), self.NFD, 1,
-             (0 if D == 0 and C == 0 else self.sms, 0 if D == 0 and C == 0 else 1)),
+             .args(pos, n, self.EPS2, 1e-3, fb, fc, self.NFD, fd), self.NFD, 1, (1, 0), ("static", ())),
         ]
         return MultiEngine(E, progs, sched, params, D, C)
 
@@ -481,8 +481,9 @@ class MultiEngine:
         for pr in progs:
             prog, gws, lws = pr[:3]
             d, c = pr[3] if len(pr) > 3 else (D, C)  # a program may name its own workers
+            s, p = pr[4] if len(pr) > 4 and sched != "monolithic" else (sched, params)  # ... and scheduler
             e = E.Engine(0)
-            e.work_items(gws, lws).scheduler(sched, params).workers(d, c)
+            e.work_items(gws, lws).scheduler(s, p).workers(d, c)
             e.program(prog)
             self.engs.append(e)
 
