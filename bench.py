@@ -18,9 +18,13 @@ Each program is one ecl_run() through the C ABI (one persistent launch).  The
 JSON line reports:
   value        work-items per second over the whole step (device-timed, inputs
                resident in HBM, L2 flushed before every step)
-  e2e          the same through the public API with pinned HOST buffers: the
-               engine copies inputs in and outputs out inside the timed region
-  roofline     the dominant kernel against its bound
+  e2e          the same from pinned HOST memory through the package's API:
+               every step copies its inputs in and its results out inside the
+               timed region, the copies on two copy streams overlapped with
+               the computation (pipeline.Overlapped); e2e_sync: the same with
+               engines that copy in, compute and copy out before returning
+  roofline     the dominant kernel against its bound, with the ncu-measured
+               DRAM traffic of a launch
   kernels      per program: time, work-items/s, own-unit rate, roofline
                fraction, scheduler overhead against a monolithic launch
                (Sec. 7.3 overhead metric) and the load balance T_FD/T_LD
@@ -84,9 +88,6 @@ class Workload:
 
     # builds self.eng (device buffers) and self.mono (monolithic launch)
     def setup(self):
-        raise NotImplementedError
-
-    def programs(self, inputs, outputs):
         raise NotImplementedError
 
     def make_engine(self, sched, params, D=0, C=0, host=False):
@@ -814,19 +815,68 @@ def run_ours(args):
     if "gemm_bf16" in kern and "gemm_split6" in kern:
         kern["gemm_split6"]["compensated_over_plain"] = kern["gemm_split6"]["ms"] / kern["gemm_bf16"]["ms"]
 
-    # end to end through host (pinned) buffers: the engine copies in, runs, copies out
+    # End to end from pinned host memory, every step: the inputs copied in, the
+    # programs run, the results copied out.  Measured two ways through the
+    # package's API: (1) pipeline.Overlapped, the copies on two copy streams
+    # overlapped with the other configurations' computation (the "e2e" value);
+    # (2) engines with host buffers, each run copying in, computing and copying
+    # out before it returns (the synchronous run of Listing 1, "e2e_sync").
+    from paper_1805_02755_gb300 import pipeline as PL
     swls = [w for w in wls if w.in_step]
     h2d = sum(t.numel() * t.element_size() for w in swls for t in w.h_in)
     d2h = sum(t.numel() * t.element_size() for w in swls for t in w.h_out)
+    # stage order: the longest computation first (the other stages' inputs move
+    # while it runs), then by output size, largest first (their results move
+    # while the shorter stages compute)
+    def dev_ms(w):
+        return sum(kern[n]["ms"] for n, _, _ in w.programs() if n in kern)
+
+    def out_bytes(w):
+        return sum(t.numel() * t.element_size() for t in w.h_out)
+
+    first = max(swls, key=dev_ms)
+    order = [first] + sorted((w for w in swls if w is not first), key=out_bytes, reverse=True)
+    ov = PL.Overlapped([PL.Stage(w.eng, zip(w.d_in, w.h_in), zip(w.h_out, w.d_out)) for w in order])
+    assert ov.bytes_in == h2d and ov.bytes_out == d2h
+    for _ in range(max(1, args.warmup)):
+        ov.run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ov.run()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+
     for _ in range(max(1, args.warmup)):
         for w in swls:
             w.host.run()
     torch.cuda.synchronize()
+    # the host link as the synchronous pass finds it: one pinned copy of the
+    # largest input, device-timed
+    big = max((t for w in swls for t in w.h_in), key=lambda t: t.numel() * t.element_size(), default=None)
+    link_gbs = None
+    if big is not None and big.numel() * big.element_size() >= (1 << 20):
+        dbig = torch.empty_like(big, device="cuda")
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        dbig.copy_(big, non_blocking=True)
+        eb.record(stream)
+        eb.synchronize()
+        link_gbs = big.numel() * big.element_size() / (ea.elapsed_time(eb) * 1e6)
+        del dbig
     t0 = time.perf_counter()
+    per_cfg = {w.name: 0.0 for w in swls}
+    per_cfg_dev = {w.name: 0.0 for w in swls}
     for _ in range(args.steps):
         for w in swls:
-            w.host.run()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tw = time.perf_counter()
+            ea.record(stream)
+            w.host.run()  # synchronous: returns with the outputs in host memory
+            eb.record(stream)
+            per_cfg[w.name] += time.perf_counter() - tw
+            eb.synchronize()
+            per_cfg_dev[w.name] += ea.elapsed_time(eb) * 1e-3
+    e2e_sync_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
 
     total_wi = sum(wi for _, _, _, wi in progs)
     value = job_rate(total_wi, world, step_ms * 1e-3)
@@ -853,7 +903,15 @@ def run_ours(args):
                    "beside_the_step": {w.name: w.config for w in wls if not w.in_step},
                    "l2": "flushed (512 MiB write) before every step", "parallelism": "replicas"},
         "e2e": {"value": job_rate(total_wi, world, e2e_s), "unit": "work-items/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+                "how": "pipeline.Overlapped: copies on two copy streams overlapped with computation",
+                "stage_order": [w.name for w in order]},
+        "e2e_sync": {"value": job_rate(total_wi, world, e2e_sync_s), "unit": "work-items/s",
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_sync_s * 1e3,
+                     "how": "engines with host buffers: each run copies in, computes, copies out, then returns",
+                     "ms_per_config": {k: v * 1e3 / args.steps for k, v in per_cfg.items()},
+                     "device_ms_per_config": {k: v * 1e3 / args.steps for k, v in per_cfg_dev.items()},
+                     "h2d_gbs_largest_input": link_gbs},
         "gpu_launches": launches * args.steps,
         "fp32_probe": probe,
         "roofline": rf,

@@ -8,7 +8,7 @@ kernel except the row-tiled GEMM, whose unit is one full row of output
 tiles); the last unit may be short when grain does not divide G.  A package
 is returned as ``(offset_wg, length_wg)``.
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here:
 
 * Static (Sec. 5.3 "Static"; Listing 2 gives n-1 proportions for n devices):
   device d < D-1 receives floor(props[d] * U) units, the product evaluated

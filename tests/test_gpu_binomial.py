@@ -4,7 +4,7 @@ Tolerance from the FP32 error analysis of the lattice: each backward level adds
 at most eps times the probability-weighted node values, whose sum is the price
 itself, so the error is ~sqrt(N) eps V (N eps V worst case); 1e-5 relative is
 applied to max(V64, 1e-4 S) so that prices far out of the money, which carry
-the rounding of S-sized leaves, are judged on the scale of S.
+the rounding of S-sized leaves, are measured on the scale of S.
 """
 import numpy as np
 import pytest

@@ -1,0 +1,58 @@
+"""pipeline.Overlapped: engines run in order with their host copies on two copy
+streams; every result lands in pinned host memory equal to the oracle's, run
+after run (the device inputs are rewritten from the host each time)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1805_02755_gb300 import build as B
+    B.build()
+    import paper_1805_02755_gb300 as E
+    return E
+
+
+def test_overlapped_stages_match_the_oracle(E, oracle_mod):
+    import torch
+    from paper_1805_02755_gb300 import pipeline as PL
+    # stage 1: Mandelbrot, output only
+    Wd, H, it = 512, 256, 200
+    m_out = torch.zeros(Wd * H, dtype=torch.int32, device="cuda")
+    m_host = torch.zeros(Wd * H, dtype=torch.int32).pin_memory()
+    e1 = E.Engine(0)
+    e1.work_items(Wd * H // 4, 256).scheduler("static", ()).workers(1, 0)
+    e1.program(E.Program("mandelbrot").out(m_out).args(m_out, Wd, H, -2.0, -1.5, 3.0 / Wd, 3.0 / H, it))
+    # stage 2: Gaussian, input and output
+    img = W.gaussian_image(192, 320)
+    w = W.gaussian_weights()
+    g_in_h = torch.from_numpy(img).pin_memory()
+    g_w_h = torch.from_numpy(w).pin_memory()
+    g_in = torch.zeros_like(g_in_h, device="cuda")
+    g_w = torch.zeros_like(g_w_h, device="cuda")
+    g_out = torch.zeros_like(g_in)
+    g_host = torch.zeros_like(g_in_h).pin_memory()
+    e2 = E.Engine(0)
+    e2.work_items(192 * 320, 128).scheduler("dynamic", (16,)).workers(4, 0)
+    e2.program(E.Program("gaussian").in_(g_in).in_(g_w).out(g_out).args(g_in, g_w, g_out, 320, 192, 31))
+    ov = PL.Overlapped([PL.Stage(e1, outputs=[(m_host, m_out)]),
+                        PL.Stage(e2, inputs=[(g_in, g_in_h), (g_w, g_w_h)], outputs=[(g_host, g_out)])])
+    assert ov.bytes_in == img.nbytes + w.nbytes and ov.bytes_out == m_host.numel() * 4 + g_host.numel() * 4
+    m_ref = oracle_mod.mandelbrot(Wd, H, -2.0, -1.5, np.float32(3.0 / Wd), np.float32(3.0 / H), it)
+    g_ref = oracle_mod.gaussian(img, w)
+    for _ in range(3):
+        g_in.zero_()  # the next run must copy the input in again
+        m_host.zero_()
+        g_host.zero_()
+        ov.run()
+        assert np.array_equal(m_host.numpy().view(np.uint32).reshape(H, Wd), m_ref)
+        g = g_host.numpy().reshape(192, 320)
+        assert np.all(np.abs(g - g_ref) <= 1e-5 * np.abs(g_ref))
+    e1.close()
+    e2.close()
