@@ -97,12 +97,55 @@ __device__ __forceinline__ void put_dup(float4 *shxy, float4 *shzm, const float4
     shzm[threadIdx.x] = make_float4(q.z, q.z, q.w, q.w);
 }
 
+// The pair loop over one tile's j-slice for a thread's two bodies: sums of
+// s d (and, for the adjoint, of m_j inv) over the slice, each body's sequence
+//   d = r_j - r_i, r2 = dx dx + (dy dy + (dz dz + eps2)), inv = rsqrt(r2),
+//   s = (m_j inv)(inv inv), sum += s d.
+struct TileSums {
+    f2 x, y, z, p;
+};
+
+template <uint32_t MODE, uint32_t SPAN>
+__device__ __forceinline__ TileSums pair_tile(const ulonglong2 *qxy, const ulonglong2 *qzm, f2 X, f2 Y, f2 Z, f2 EPS)
+{
+    f2 TX = 0, TY = 0, TZ = 0, TP = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < SPAN; ++k) {
+        const ulonglong2 xy = qxy[k], zm = qzm[k];
+        const f2 dx = sub2(xy.x, X), dy = sub2(xy.y, Y), dz = sub2(zm.x, Z);
+        const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, EPS)));
+        float r0, r1;
+        upk(r2, r0, r1);
+        const f2 inv = pk(rsqrtf(r0), rsqrtf(r1));
+        const f2 mi = mul2(zm.y, inv);
+        if (MODE == NB_ADJ) TP = add2(TP, mi);
+        const f2 sc = mul2(mi, mul2(inv, inv));
+        TX = fma2(sc, dx, TX);
+        TY = fma2(sc, dy, TY);
+        TZ = fma2(sc, dz, TZ);
+    }
+    return TileSums{TX, TY, TZ, TP};
+}
+
+// The same as a call, for the persistent form: a function of its own gets its
+// own register allocation.  Inlined into the claim loop (72 registers at 3
+// CTAs per SM, the driver's loop state live around it) the pair loop spent
+// about four register moves per pair; called once per tile it spends none,
+// while the caller saves a few values around each call.  The monolithic form
+// keeps the inlined loop, its faster form.
+template <uint32_t MODE, uint32_t SPAN>
+__device__ __noinline__ TileSums pair_tile_call(const ulonglong2 *qxy, const ulonglong2 *qzm, f2 X, f2 Y, f2 Z,
+                                                f2 EPS)
+{
+    return pair_tile<MODE, SPAN>(qxy, qzm, X, Y, Z, EPS);
+}
+
 // Force loop: thread t owns bodies (b, b + lws/2) of the work-group, b =
 // t % (lws/2), and the j-slice t / (lws/2); both bodies advance together in
 // packed FP32x2 arithmetic, each exactly as the scalar sequence
 //   d = r_j - r_i, r2 = dx dx + (dy dy + (dz dz + eps2)), inv = rsqrt(r2),
 //   s = (m_j inv)(inv inv), a += s d.
-template <uint32_t MODE>
+template <uint32_t MODE, bool CALL>
 struct ForceBody {
     static constexpr uint32_t kThreads = kFBlock;
     using Params = NBodyParams;
@@ -156,24 +199,11 @@ struct ForceBody {
             const bool more = tile + 1 < tb;
             float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
             if (more) nxt = tile_body(p.pos, p.n, tile + 1);
-            f2 TX = 0, TY = 0, TZ = 0, TP = 0;
             const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + cur * kFTile + s * SPAN);
             const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + cur * kFTile + s * SPAN);
-#pragma unroll
-            for (uint32_t k = 0; k < SPAN; ++k) {
-                const ulonglong2 xy = qxy[k], zm = qzm[k];
-                const f2 dx = sub2(xy.x, X), dy = sub2(xy.y, Y), dz = sub2(zm.x, Z);
-                const f2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, EPS)));
-                float r0, r1;
-                upk(r2, r0, r1);
-                const f2 inv = pk(rsqrtf(r0), rsqrtf(r1));
-                const f2 mi = mul2(zm.y, inv);
-                if (MODE == NB_ADJ) TP = add2(TP, mi);
-                const f2 sc = mul2(mi, mul2(inv, inv));
-                TX = fma2(sc, dx, TX);
-                TY = fma2(sc, dy, TY);
-                TZ = fma2(sc, dz, TZ);
-            }
+            const TileSums T = CALL ? pair_tile_call<MODE, SPAN>(qxy, qzm, X, Y, Z, EPS)
+                                    : pair_tile<MODE, SPAN>(qxy, qzm, X, Y, Z, EPS);
+            const f2 TX = T.x, TY = T.y, TZ = T.z, TP = T.p;
             A[0] = add2(A[0], TX);
             A[kFBlock] = add2(A[kFBlock], TY);
             A[2 * kFBlock] = add2(A[2 * kFBlock], TZ);
@@ -462,14 +492,14 @@ __global__ void __launch_bounds__(kFBlock + 32, 3) k_nbody_force(NBodyParams prm
 {
     extern __shared__ __align__(16) float4 fsm[];
     __shared__ uint32_t flag;
-    ForceBody<MODE> b;
+    ForceBody<MODE, FORM == DRIVE_QUEUE> b;
     b.p = prm;
     b.shxy = fsm;
     b.shzm = fsm + 2 * kFTile;
     b.red = fsm;
     b.acc = reinterpret_cast<f2 *>(fsm + 4 * kFTile);
     b.flag = &flag;
-    drive_ws<ForceBody<MODE>, FORM>(s, b);
+    drive_ws<ForceBody<MODE, FORM == DRIVE_QUEUE>, FORM>(s, b);
 }
 
 __global__ void __launch_bounds__(kBlock + 32) k_nbody_energy(EnergyParams prm, SchedArgs s)
