@@ -6,10 +6,11 @@
 // lattice holds nodes j = 0..t; node j lives in lane j / R, register slot
 // j % R, where the width R steps down 64, 56, 48, ..., 2, 1 as the lattice
 // shrinks; a lattice starts at the narrowest width that holds its leaves
-// (each width's code exists once and is entered by index).  A backward step needs node j+1: in the same lane except for the
-// last slot, which one shuffle per level brings from the next lane.  When
-// the live nodes fit in the next width the warp repacks its registers
-// through a padded shared buffer, so ~90% of the computed slots stay live.
+// (each width's code exists once and is entered by index).  A backward step
+// needs node j+1: in the same lane except for the last slot, which one
+// shuffle per level brings from the next lane.  When the live nodes fit in
+// the next width the warp repacks its registers through a padded shared
+// buffer, so ~90% of the computed slots stay live.
 //
 // Arithmetic (exact in real numbers, arranged for FP32):
 //   p = 1/2 + q,  q = (expm1(r dt) - 2 sinh^2(a/2)) / (2 sinh a),  a = sigma sqrt(dt)
@@ -35,12 +36,18 @@
 // difference operator (shift - identity) are both shift-invariant, so they
 // commute, and the N coefficient terms of the vega tree add up to
 //   N 2q' (B_1 - B_0)   (B_1, B_0: the two nodes of level 1, same scaling).
-// So delta, the leaf part of vega and the price are three independent
-// lattices of the same recursion: the warp runs the price code three times
-// with different leaves, keeps B_1 - B_0 from the price pass, and
-//   vega = root(vega leaves) + N 2q' (B_1 - B_0).
-// This is the same derivative; in FP32 emulation its error matches the
-// level-by-level form (~1e-6 relative).
+// So delta and the leaf part of vega are the same recursion applied to the
+// leaf derivatives, linear functionals of the leaves.  One reverse (adjoint)
+// pass gives the weights A of every node of level N - 1 in the root
+// (A = 1 at the root, A'_j = (A_j + A_{j-1}) + 2q (A_{j-1} - A_j) outwards),
+// and both become dot products of A with the leaf derivatives pushed back
+// one level; with B_1 - B_0 kept from the price pass,
+//   vega = <A, vega leaves'> + N 2q' (B_1 - B_0).
+// Stored in reverse node order the adjoint recursion is the backward level
+// itself, so the price pass and the adjoint pass run on one copy of the
+// level code.  In FP32 emulation of this arithmetic against the FP64 oracle,
+// options of depth 1900..2048 show ~1.7e-6 relative error in the price,
+// ~0.9e-6 in delta and ~1.8e-6 in vega.
 #include <cuda_runtime.h>
 
 #include "ecl_internal.h"
