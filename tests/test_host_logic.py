@@ -1,4 +1,5 @@
-"""Host-side logic that needs no GPU: batch table layout and batch splitting."""
+"""Host-side logic that needs no GPU: batch table layout and batch splitting,
+the Chrome trace, and the bench's balance, efficiency and rate helpers."""
 import numpy as np
 
 
@@ -40,3 +41,47 @@ def test_chrome_trace_of_package_records(tmp_path):
     assert ev[1]["args"] == {"off_wg": 4, "len_wg": 4, "smid": 0}
     assert json.load(open(path)) == tr
     assert E.chrome_trace(st[:0])["traceEvents"] == []
+
+
+def _pkg_stats(rows):
+    import paper_1805_02755_gb300 as E
+    a = np.zeros(len(rows), dtype=E.PKG_STAT_DTYPE)
+    for i, (dev, t0, t1) in enumerate(rows):
+        a[i]["device"], a[i]["t0_ns"], a[i]["t1_ns"] = dev, t0, t1
+    return a
+
+
+def _worker_stats(rows):
+    import paper_1805_02755_gb300 as E
+    a = np.zeros(len(rows), dtype=E.WORKER_STAT_DTYPE)
+    for i, (busy, chunks) in enumerate(rows):
+        a[i]["busy_ns"], a[i]["chunks"], a[i]["cta"] = busy, chunks, i
+    return a
+
+
+def test_balance_is_first_over_last_device_finish():
+    """Sec. 7.3 balance T_FD / T_LD: each device's last package end, from the
+    first package start; one device balances trivially."""
+    import bench
+    st = _pkg_stats([(0, 100, 300), (1, 100, 500), (0, 300, 400), (1, 120, 200)])
+    assert bench.balance_of(st) == (400 - 100) / (500 - 100)
+    assert bench.balance_of(_pkg_stats([(0, 10, 50), (0, 50, 90)])) == 1.0
+    assert bench.balance_of(_pkg_stats([])) is None
+
+
+def test_worker_efficiency_and_the_grid_form():
+    """Mean over max busy time of the persistent CTAs; none for Static over one
+    device, which runs as a grid of one-chunk CTAs."""
+    import bench
+    ws = _worker_stats([(100, 3), (50, 2), (150, 4)])
+    assert bench.worker_efficiency(ws, dict(devices=2, ctas_per_device=2, ctas=4)) == 100 / 150
+    grid = _worker_stats([(30, 1), (90, 1)])
+    assert bench.worker_efficiency(grid, dict(devices=1, ctas_per_device=2, ctas=2)) is None
+    # one device of persistent CTAs with several chunks each is not the grid form
+    assert bench.worker_efficiency(ws, dict(devices=1, ctas_per_device=3, ctas=3)) == 100 / 150
+
+
+def test_job_rate_counts_every_rank():
+    import bench
+    assert bench.job_rate(1000, 4, 2.0) == 2000.0
+    assert bench.max_over_ranks(1.5, 1) == 1.5
