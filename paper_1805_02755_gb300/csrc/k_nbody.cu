@@ -502,6 +502,9 @@ __global__ void __launch_bounds__(kFBlock + 32, 3) k_nbody_force(NBodyParams prm
     drive_ws<ForceBody<MODE, FORM == DRIVE_QUEUE>, FORM>(s, b);
 }
 
+// One instance per launch form (DRIVE_MONO, DRIVE_QUEUE), each with a single
+// inlined copy of the body.
+template <int FORM>
 __global__ void __launch_bounds__(kBlock + 32) k_nbody_energy(EnergyParams prm, SchedArgs s)
 {
     __shared__ float4 sh[kTile];
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(kBlock + 32) k_nbody_energy(EnergyParams prm, 
     b.p = prm;
     b.sh = sh;
     b.dsh = dsh;
-    drive_ws(s, b);
+    drive_ws<EnergyBody, FORM>(s, b);
 }
 
 __global__ void __launch_bounds__(kBlock + 32) k_nbody_fd(FDParams prm, SchedArgs s)
@@ -747,7 +750,7 @@ ecl_status v_energy(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err
 ecl_status l_energy(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
     const uint64_t G = c.gws / c.lws;
-    char *ws = (char *)workspace_get(c.ws, 256 + G * kESeg * sizeof(double), err, (const void *)k_nbody_energy, c.stream);
+    char *ws = (char *)workspace_get(c.ws, 256 + G * kESeg * sizeof(double), err, (const void *)k_nbody_energy<DRIVE_QUEUE>, c.stream);
     if (!ws) return ECL_ERR_CUDA;
     EnergyParams p{};
     p.pos = a.buf<const float4>(0);
@@ -758,11 +761,14 @@ ecl_status l_energy(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std:
     p.partial = (double *)(ws + 256);
     p.G = G;
     p.lws = c.lws;
-    k_nbody_energy<<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
+    if (s.mode == MODE_MONO)
+        k_nbody_energy<DRIVE_MONO><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
+    else
+        k_nbody_energy<DRIVE_QUEUE><<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
 }
 
-int o_energy() { return occ((const void *)k_nbody_energy); }
+int o_energy() { return occ((const void *)k_nbody_energy<DRIVE_QUEUE>); }
 
 // ---- nbody_fd: in_pos, bodies, esp_sqr, h, body[], comp[], count, out[] (double)
 ecl_status v_fd(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
@@ -905,7 +911,7 @@ extern "C" ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, floa
     s.grain = 1;
     s.units = G;
     s.mono_nchunks = (uint32_t)(G * kESeg);
-    k_nbody_energy<<<(unsigned)(G * kESeg), kBlock + 32, 0, st>>>(p, s);
+    k_nbody_energy<DRIVE_MONO><<<(unsigned)(G * kESeg), kBlock + 32, 0, st>>>(p, s);
     if (cudaGetLastError() != cudaSuccess) return ECL_ERR_CUDA;
     return ECL_OK;
 }
