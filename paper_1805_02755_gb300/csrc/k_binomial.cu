@@ -70,7 +70,6 @@ struct BinoParams {
 
 struct Lat {
     float q2;      // 2q
-    int active;    // live nodes at the current level
     int rescale;   // levels since the last rescale
     int shift;     // power of two still to remove from the result
 };
