@@ -181,6 +181,23 @@ def test_every_scheduler_bit_exact_and_covers_once(E, torch, oracle_mod, sched, 
     eng.close()
 
 
+@pytest.mark.parametrize("sched,params,D,C,Wd,H", [
+    ("static", (), 300, 1, 1000, 37),          # more devices than work-groups: empty packages
+    ("static_rev", (), 64, 2, 1000, 37),
+    ("hguided", (1000.0, 1.0), 16, 3, 1000, 37),  # every package at the minimum size
+    ("dynamic", (4,), 32, 4, 64, 4),           # one work-group in all (64 x 4 px, lws 64)
+    ("hguided", (2.0, 1.0), 8, 8, 64, 4),
+])
+def test_degenerate_schedules_cover_once(E, torch, oracle_mod, sched, params, D, C, Wd, H):
+    it = 150
+    eng, img, cov, G, r = run(E, torch, Wd, H, it, sched, params, D, C, lws=64, coverage=True)
+    assert np.array_equal(img, oracle_img(oracle_mod, Wd, H, it, r))
+    assert (cov.cpu().numpy() == 1).all()
+    st = eng.stats()
+    assert int(st["len_wg"].sum()) == G
+    eng.close()
+
+
 def test_repeated_runs_reset_the_queue(E, torch, oracle_mod):
     Wd, H, it = 512, 512, 64
     out = torch.zeros(Wd * H, dtype=torch.int32, device="cuda")
