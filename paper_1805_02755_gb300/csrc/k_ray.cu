@@ -97,7 +97,6 @@ __device__ __forceinline__ bool blocked(const RayScene &sc, int ns, float ox, fl
 }
 
 struct RayBody {
-    static constexpr uint32_t kThreads = kBlock;
     using Params = RayParams;
     Params p;
     const RayScene *sc;
