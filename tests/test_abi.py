@@ -86,3 +86,48 @@ def test_null_handles(E):
     assert L.ecl_engine_create(None, 0, None) == E.ECL_ERR_ARG
     L.ecl_engine_destroy(None)
     assert L.ecl_last_error(None) == b"NULL engine"
+
+
+def _table2():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table2_properties.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, lws, rw, outp, nargs = line.split()
+            r, w = (int(v) for v in rw.split(":"))
+            rows[name] = dict(lws=int(lws), reads=r, writes=w, out=outp, args=int(nargs))
+    return rows
+
+
+def _kernel_args(E, name):
+    out = []
+    while E.ecl_kernel_arg(name, len(out)) is not None:
+        out.append(E.ecl_kernel_arg(name, len(out)))
+    return out
+
+
+@pytest.mark.parametrize("name", ["gaussian", "ray", "mandelbrot", "nbody"])
+def test_table2_argument_and_buffer_counts(E, name):
+    """The built-in kernels of these benchmarks take Table 2's number of
+    arguments and of read and written buffers."""
+    want = _table2()[name]
+    args = _kernel_args(E, name)
+    reads = sum(1 for k, _ in args if k == E.ECL_ARG_BUF_IN)
+    writes = sum(1 for k, _ in args if k in (E.ECL_ARG_BUF_OUT, E.ECL_ARG_BUF_OUT_OPT))
+    assert (len(args), reads, writes) == (want["args"], want["reads"], want["writes"])
+
+
+def test_table2_binomial_differs_as_documented(E):
+    """Table 2's binomial prices one fixed-depth lattice per 255-wide
+    work-group (5 arguments, 1:1 buffers, out 1:255); this one prices a batch
+    of options of uneven depth (1..2048), one warp each, with delta and vega:
+    9 arguments, 5 read buffers (S, K, T, sigma, depth), price and greeks
+    written."""
+    want = _table2()["binomial"]
+    args = _kernel_args(E, "binomial")
+    reads = sum(1 for k, _ in args if k == E.ECL_ARG_BUF_IN)
+    writes = sum(1 for k, _ in args if k in (E.ECL_ARG_BUF_OUT, E.ECL_ARG_BUF_OUT_OPT))
+    assert (len(args), reads, writes) == (9, 5, 2)
+    assert (len(args), reads, writes) != (want["args"], want["reads"], want["writes"])
