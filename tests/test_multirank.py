@@ -70,5 +70,14 @@ def test_reference_arm_prints_on_rank_zero_only(rank, prints):
         assert len(lines) == 1
         d = json.loads(lines[0])
         assert d["impl"] == "reference" and d["value"] > 0
+        # the line the driver reads: the same keys as the kernel arm's, the
+        # oracle described, and no host-device copies
+        for k in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                  "vs_baseline", "dtype", "data", "config"):
+            assert k in d, k
+        assert d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True  # warm-up raised to 3
+        assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+        assert d["cpu_baseline"]["value"] == d["value"]
+        assert d["e2e"] == dict(value=d["value"], unit=d["unit"], h2d_bytes_per_step=0, d2h_bytes_per_step=0)
     else:
         assert lines == []
