@@ -1,12 +1,13 @@
 """Builds libecl.so in-tree with nvcc for sm_103a (no torch extension machinery).
 
 Each .cu file is compiled to an object in parallel, then the objects are
-linked into one shared library next to this file.  The Mandelbrot unit is
-and ray-tracing units are compiled with -fmad=false (their results must
-match a correctly rounded host evaluation bit for bit).  The NBody unit is compiled with -ftz=true: every
-FP32 value there is far from the subnormal range (r^2 >= eps^2 > 0), and
-without subnormal handling rsqrtf is the bare hardware reciprocal square
-root instead of a range check, a scaling and the root.
+linked into one shared library next to this file.  The Mandelbrot and
+ray-tracing units are compiled with -fmad=false (their results must match a
+correctly rounded host evaluation bit for bit).  The NBody unit is compiled
+with -ftz=true: every FP32 value there is far from the subnormal range
+(r^2 >= eps^2 > 0), and without subnormal handling rsqrtf is the bare
+hardware reciprocal square root instead of a range check, a scaling and the
+root.
 """
 from __future__ import annotations
 
