@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/ecl.h"
@@ -155,5 +156,13 @@ const KernelDesc *find_kernel(const char *name);
 // before they exit.
 void *workspace_get(Workspace *ws, size_t bytes, std::string &err, const void *owner = nullptr,
                     cudaStream_t stream = 0);
+
+// Raises kernel `fn`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per device: the attribute belongs to the function on one
+// device, so a process with engines on several GPUs sets it on each.  `done`
+// holds one bit per device ordinal (ordinals from 64 up are set every call).
+// Setting it twice is harmless, so host threads that race here need no lock.
+// Returns false, with the CUDA error cleared, when the driver refuses.
+bool smem_limit_once(const void *fn, int bytes, std::atomic<unsigned long long> &done);
 
 }  // namespace ecl

@@ -340,16 +340,8 @@ constexpr size_t kSmem31 = sizeof(float) * kNIN * kSW;
 
 bool set_smem_attr()
 {
-    static bool done = false;
-    if (!done) {
-        if (cudaFuncSetAttribute(k_gauss31, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem31) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        done = true;
-    }
-    return true;
+    static std::atomic<unsigned long long> done{0};
+    return smem_limit_once((const void *)k_gauss31, (int)kSmem31, done);
 }
 
 int ctas_per_sm()

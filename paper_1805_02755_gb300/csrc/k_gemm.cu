@@ -366,15 +366,8 @@ __global__ void __launch_bounds__(256) k_cast(CastParams prm, SchedArgs s)
 // ---------------------------------------------------------------- host side
 bool set_smem()
 {
-    static bool done = false;
-    if (!done) {
-        if (cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        done = true;
-    }
-    return true;
+    static std::atomic<unsigned long long> done{0};
+    return smem_limit_once((const void *)k_gemm, (int)SMEM_BYTES, done);
 }
 
 int gemm_ctas_per_sm()

@@ -389,8 +389,8 @@ __global__ void k_split6(const float *A, const float *B, __nv_bfloat16 *a3, __nv
 // ---------------------------------------------------------------- host side
 bool set_smem()
 {
-    return cudaFuncSetAttribute(k_gemm6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) ==
-           cudaSuccess;
+    static std::atomic<unsigned long long> done{0};
+    return smem_limit_once((const void *)k_gemm6, (int)SMEM_BYTES, done);
 }
 
 int ctas_per_sm()

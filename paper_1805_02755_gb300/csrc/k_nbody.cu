@@ -541,10 +541,9 @@ int occ(const void *fn, int block = kBlock + 32, size_t smem = 0)
 template <uint32_t MODE>
 bool force_smem_ok()
 {
-    return cudaFuncSetAttribute((const void *)k_nbody_force<MODE, DRIVE_QUEUE>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem) == cudaSuccess &&
-           cudaFuncSetAttribute((const void *)k_nbody_force<MODE, DRIVE_MONO>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem) == cudaSuccess;
+    static std::atomic<unsigned long long> queue_done{0}, mono_done{0};
+    return smem_limit_once((const void *)k_nbody_force<MODE, DRIVE_QUEUE>, (int)kFSmem, queue_done) &&
+           smem_limit_once((const void *)k_nbody_force<MODE, DRIVE_MONO>, (int)kFSmem, mono_done);
 }
 
 template <uint32_t MODE>

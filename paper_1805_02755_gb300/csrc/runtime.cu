@@ -26,6 +26,23 @@ struct Workspace {
     const void *owner = nullptr;  // kernel whose counters the memory holds
 };
 
+bool smem_limit_once(const void *fn, int bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    done.fetch_or(bit, std::memory_order_release);
+    return true;
+}
+
 void *workspace_get(Workspace *ws, size_t bytes, std::string &err, const void *owner, cudaStream_t stream)
 {
     if (ws->bytes >= bytes) {
