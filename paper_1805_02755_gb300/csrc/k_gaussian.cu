@@ -4,11 +4,11 @@
 // Work-item g produces pixel g of the row-major image, so a package of
 // work-groups is a range of pixels: a band of rows with possibly partial
 // first and last rows.  The kernel splits a package into chunks of
-// (32-row band) x (256-column tile).  A chunk runs the vertical pass first
-// (one thread per column of the tile plus its 2r halo columns; the 32
-// outputs of a column slide down the input rows in registers, every input
-// value read once from global memory) into a shared-memory tile, then the
-// horizontal pass (four consecutive outputs per thread, 128-bit shared
+// (32-row band) x (224 output columns; 256 staged with the halo).  A chunk
+// runs the vertical pass first (one thread per column of the tile plus its
+// 2r halo columns; the 32 outputs of a column slide down the input rows in
+// registers, each staged value read once) into a shared-memory tile, then
+// the horizontal pass (four consecutive outputs per thread, 128-bit shared
 // loads and 128-bit stores).  Only pixels inside the package's range are
 // written, so packages that split a row are handled exactly.
 //
