@@ -123,14 +123,18 @@ typedef struct ecl_binomial_instance {
 
 /* ---------------------------------------------------------------- engine */
 
-/* Creates an engine on CUDA device `device_ordinal`.  `cuda_stream` is a
+/* Creates an engine on CUDA device `device_ordinal` (Sec. 6 and Listing 1:
+ * the engine manages the devices, the work sizes, the scheduler and the
+ * execution statistics; `engine.use(...)` picks the devices, here one GPU
+ * whose CTAs are split into devices by ecl_workers).  `cuda_stream` is a
  * cudaStream_t (NULL = the legacy default stream); every launch and copy
  * of the engine is ordered on it.  Allocates the queue and statistics
  * memory.  Errors: ECL_ERR_ARG (e NULL), ECL_ERR_CUDA. */
 ecl_status ecl_engine_create(ecl_engine **e, int device_ordinal, void *cuda_stream);
 
 /* Waits for the engine's stream, then frees the engine, its programs and
- * its device memory.  NULL is ignored. */
+ * its device memory (the end of the engine's scope in Listings 1 and 2,
+ * where the engine owns the program it was given).  NULL is ignored. */
 void ecl_engine_destroy(ecl_engine *e);
 
 /* Replaces the stream used by later calls. */
@@ -146,7 +150,10 @@ ecl_status ecl_work_items(ecl_engine *e, uint64_t gws, uint32_t lws);
  * out-of-range parameters (checked again at run time against D and G). */
 ecl_status ecl_scheduler(ecl_engine *e, ecl_sched_kind kind, const double *params, int nparams);
 
-/* Number of devices D and CTAs per device C.  0 = automatic: for most
+/* Number of devices D and CTAs per device C (Sec. 4.2 Device module and
+ * Listing 2's engine.use(ecl::Device(...), ...): the devices that share
+ * the NDRange; Sec. 5.1: one thread drives each device, here a group of
+ * C persistent CTAs takes that role).  0 = automatic: for most
  * kernels C = 1 and D = every CTA that fits on the GPU at once; for the
  * GEMM D = 4 groups sharing the SMs.  D*C beyond what is resident at
  * once is allowed (the queue never waits for a CTA that has not started)
@@ -175,7 +182,10 @@ ecl_status ecl_run(ecl_engine *e);
 ecl_status ecl_synchronize(ecl_engine *e);
 
 /* Copies up to `cap` package records of the last run into `out` (host
- * memory), in hand-out order, and stores the count in *n.  Synchronises.
+ * memory), in hand-out order, and stores the count in *n (the data the
+ * paper's Introspector module extracts from a run, Sec. 5.3's figure of
+ * packages per scheduler; Sec. 7.3 derives balance from the devices'
+ * finish times).  Synchronises.
  * Monolithic runs have no packages (*n = 0). */
 ecl_status ecl_stats(ecl_engine *e, ecl_pkg_stat *out, size_t cap, size_t *n);
 
@@ -222,8 +232,10 @@ ecl_status ecl_plan(ecl_sched_kind kind, const double *params, int nparams, uint
                     uint32_t devices, uint64_t *off, uint64_t *len, uint32_t *device, size_t cap,
                     size_t *n, char *errbuf, size_t errlen);
 
-/* Text of the most recent error of the engine ("" when none).  The pointer
- * stays valid until the next failing call, ecl_clear_errors or destroy. */
+/* Text of the most recent error of the engine ("" when none): the
+ * has_errors() / get_errors() lines at the end of Listing 1, as a latched
+ * message.  The pointer stays valid until the next failing call,
+ * ecl_clear_errors or destroy. */
 const char *ecl_last_error(const ecl_engine *e);
 
 /* Number of errors seen since creation or the last clear, and clearing. */
@@ -237,7 +249,10 @@ ecl_status ecl_kernel_occupancy(int device_ordinal, const char *kernel_name,
 
 /* ---------------------------------------------------------------- program */
 
-/* Creates a program bound to one built-in kernel (see the list below).
+/* Creates a program bound to one built-in kernel (see the list below): the
+ * Program of Sec. 4.2 (inputs, outputs, a kernel and an output pattern)
+ * and Listing 1's `ecl::Program program; program.kernel(src, name)`, with
+ * the name selecting a compiled kernel instead of OpenCL source.
  * Errors: ECL_ERR_ARG, ECL_ERR_KERNEL (unknown name). */
 ecl_status ecl_program_create(ecl_program **p, const char *kernel_name);
 
@@ -300,6 +315,10 @@ const char *ecl_kernel_name(int i);
  * loads the library holds it (512 KiB + 256 B) until the process exits.  The
  * first call on a device looks its address up (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
+ * The address is kept per device ordinal for the life of the process: it
+ * does not survive cudaDeviceReset (or any other teardown of the device's
+ * primary context), after which this entry point must not be called again
+ * in the same process.
  * Every call on a device shares the one array and each call clears its
  * counter first, so calls whose work overlaps on the GPU (other streams,
  * other host threads) race: order them on one stream.  Asynchronous like

@@ -314,9 +314,32 @@ def ecl_kernel_arg(kernel_name: str, index: int):
     return kind.value, name.value.decode()
 
 
+def _noalloc_check(pos4, n: int, out_energy) -> None:
+    """The C entry point sees bare addresses and cannot check buffer sizes:
+    pos4 must be a contiguous float32 tensor of at least 4 n values and
+    out_energy a contiguous float64 tensor of at least one value, both on the
+    current CUDA device.  Raises ValueError otherwise."""
+    import torch
+    for name, t, dt, need in (("pos4", pos4, torch.float32, 4 * max(int(n), 0)),
+                              ("out_energy", out_energy, torch.float64, 1)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != dt:
+            raise ValueError("%s must be %s, not %s" % (name, dt, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if t.numel() < need:
+            raise ValueError("%s holds %d values, %d needed" % (name, t.numel(), need))
+    for name, t in (("pos4", pos4), ("out_energy", out_energy)):
+        if t.device.type != "cuda" or t.device.index != torch.cuda.current_device():
+            raise ValueError("%s must be on the current CUDA device" % name)
+
+
 def ecl_nbody_energy_noalloc(pos4, n: int, eps2: float, out_energy, cuda_stream=None) -> None:
     """Potential energy into out_energy (device double[1]) without allocating;
-    see include/ecl.h for the limits (n <= 524288, one shared scratch array)."""
+    see include/ecl.h for the limits (n <= 524288, one shared scratch array).
+    The tensors are checked first (dtype, contiguity, size, device)."""
+    _noalloc_check(pos4, n, out_energy)
     _check(lib().ecl_nbody_energy_noalloc(_vp(pos4.data_ptr()), n, eps2, _vp(out_energy.data_ptr()),
                                           _vp(_stream_handle(cuda_stream))))
 

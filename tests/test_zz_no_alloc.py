@@ -41,7 +41,10 @@ def regular_energy(E, x, n):
     return float(e.item())
 
 
-@pytest.mark.parametrize("n", [3, 1000, 65536])
+# 524288 bodies fill the scratch exactly (8192 work-groups x 8 segments =
+# 65536 partials); 524288 - 37 also needs all 8192 work-groups, the last one
+# holding 27 bodies.
+@pytest.mark.parametrize("n", [3, 1000, 65536, 524288 - 37, 524288])
 def test_noalloc_energy_matches_regular_twice(E, n):
     import torch
     pos, _ = W.nbody_bodies(n, seed=600 + n)
@@ -52,12 +55,25 @@ def test_noalloc_energy_matches_regular_twice(E, n):
         E.ecl_nbody_energy_noalloc(x, n, EPS2, out)
         torch.cuda.synchronize()
         got = float(out.item())
-        assert math.isclose(got, want, rel_tol=RTOL), (got, want)
+        # same pair terms, partials summed in the same fixed order: the same bits
+        assert got == want, (got, want)
+        assert math.isclose(got, want, rel_tol=RTOL)
+
+
+def test_noalloc_energy_matches_the_oracle(E, oracle_mod):
+    import torch
+    n = 1000
+    pos, _ = W.nbody_bodies(n, seed=1600)
+    x = torch.from_numpy(pos).cuda()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    E.ecl_nbody_energy_noalloc(x, n, EPS2, out)
+    torch.cuda.synchronize()
+    assert math.isclose(float(out.item()), oracle_mod.nbody_energy(pos, EPS2), rel_tol=RTOL)
 
 
 def test_noalloc_energy_rejects_sizes_beyond_the_scratch(E):
     import torch
-    x = torch.zeros((16, 4), device="cuda")
+    x = torch.zeros((524288 + 64, 4), device="cuda")  # large enough for the binding's size check
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(E.EclError) as ei:
         E.ecl_nbody_energy_noalloc(x, 524288 + 64, EPS2, out)
