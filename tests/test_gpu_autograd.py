@@ -70,24 +70,65 @@ def test_binomial_backward_matches_oracle_and_fd(A, oracle_mod):
     assert (np.abs(price.detach().cpu().numpy() - rp) <= 1e-5 * np.maximum(rp, 1e-4 * Sn)).all()
     assert (np.abs(S.grad.cpu().numpy() - wn * rd) <= 1e-5 * wn * np.maximum(np.abs(rd), 1e-4)).all()
     assert (np.abs(sig.grad.cpu().numpy() - wn * rv) <= 1e-5 * wn * np.maximum(np.abs(rv), 1e-4 * Sn)).all()
-    # central differences of the GPU price (FP32) with a bump of 1% of S, against
-    # the oracle's central differences (FP64) at the same bumped spots: each
-    # price is within 1e-5 max(V, 1e-4 S), so the quotients agree to
-    # 2e-5 max(V, 1e-4 S) / (2h) = 1e-3 max(V/S, 1e-4)
-    with torch.no_grad():
-        h = 0.01 * t["S"]
-        sp, sm = t["S"] + h, t["S"] - h
-        up = A.binomial_price(sp, t["K"], t["T"], t["sigma"], t["steps"], o["r"])
-        dn = A.binomial_price(sm, t["K"], t["T"], t["sigma"], t["steps"], o["r"])
-        fd = ((up - dn) / (sp - sm)).cpu().numpy()
-    spn, smn = sp.cpu().numpy(), sm.cpu().numpy()
-    rup = oracle_mod.binomial(spn, o["K"], o["T"], o["sigma"], o["steps"], o["r"])[0]
-    rdn = oracle_mod.binomial(smn, o["K"], o["T"], o["sigma"], o["steps"], o["r"])[0]
-    fd_ref = (rup - rdn) / (spn.astype(np.float64) - smn.astype(np.float64))
-    assert (np.abs(fd - fd_ref) <= 1e-3 * np.maximum(rp / Sn, 1e-4) + 1e-6).all()
-    # the lattice price is piecewise linear in S: the quotient is delta averaged over
-    # [S - h, S + h], within gamma * h of delta at S
-    assert np.median(np.abs(fd - rd)) < 1e-2
+    # Central differences of the GPU prices against the oracle's at the same
+    # FP32 bumps, and against the GPU's own delta and vega, option by option.
+    K, T, N = (o[k].astype(np.float64) for k in ("K", "T", "steps"))
+    sg = o["sigma"].astype(np.float64)
+
+    def gpu_price(Sv, sigv):
+        with torch.no_grad():
+            return A.binomial_price(torch.from_numpy(Sv).cuda(), t["K"], t["T"], torch.from_numpy(sigv).cuda(),
+                                    t["steps"], o["r"]).cpu().numpy().astype(np.float64)
+
+    def kinks(Slo, Shi, siglo, sighi):
+        # options with a leaf whose payoff S u^j d^(N-j) - K changes sign
+        # between the two bumped inputs (the lattice price has a kink there)
+        out = np.zeros(len(K), bool)
+        for i in range(len(K)):
+            m = 2.0 * np.arange(N[i] + 1) - N[i]
+            sdt = np.sqrt(T[i] / N[i])
+            a = Slo[i] * np.exp(siglo[i] * sdt * m) - K[i]
+            b = Shi[i] * np.exp(sighi[i] * sdt * m) - K[i]
+            out[i] = ((a * b <= 0) | (np.minimum(np.abs(a), np.abs(b)) <= 1e-6 * K[i])).any()
+        return out
+
+    def fd_pair(Sp, Sm, sigp, sigm, x_p, x_m):
+        up, dn = gpu_price(Sp, sigp), gpu_price(Sm, sigm)
+        rup = oracle_mod.binomial(Sp, o["K"], o["T"], sigp, o["steps"], o["r"])[0]
+        rdn = oracle_mod.binomial(Sm, o["K"], o["T"], sigm, o["steps"], o["r"])[0]
+        dx = x_p.astype(np.float64) - x_m.astype(np.float64)
+        # each GPU price is within 1e-5 max(V, 1e-4 S) of the oracle's
+        noise = 1e-5 * (np.maximum(rup, 1e-4 * Sp) + np.maximum(rdn, 1e-4 * Sm)) / dx
+        return (up - dn) / dx, (rup - rdn) / dx, noise
+
+    Sf = o["S"]
+    # delta: S bumped by 0.1%.  Without a kink in [S-, S+] the lattice price is
+    # linear in S, so the oracle quotient equals the oracle delta; with one,
+    # the quotient is delta averaged over the bump and the oracle measures
+    # the gap.
+    Sp = (Sf + np.float32(1e-3) * Sf).astype(np.float32)
+    Sm = (Sf - np.float32(1e-3) * Sf).astype(np.float32)
+    fd, fd_ref, noise = fd_pair(Sp, Sm, o["sigma"], o["sigma"], Sp, Sm)
+    assert (np.abs(fd - fd_ref) <= noise).all(), (np.abs(fd - fd_ref) / noise).max()
+    kd = kinks(Sm.astype(np.float64), Sp.astype(np.float64), sg, sg)
+    assert (~kd).sum() >= 64
+    assert np.allclose(fd_ref[~kd], rd[~kd], rtol=1e-9, atol=1e-12)
+    dg = S.grad.cpu().numpy().astype(np.float64) / wn
+    gap = np.where(kd, np.abs(rd - fd_ref), 0.0)
+    assert (np.abs(dg - fd) <= gap + noise + 1e-5 * np.maximum(np.abs(rd), 1e-4)).all()
+    # vega: sigma bumped by 1e-3 (FP32-representable bumps); the price is
+    # smooth in sigma between kinks, and the oracle's own quotient gives the
+    # truncation gap |vega - quotient| of this lattice at these bumps
+    sp = (o["sigma"] + np.float32(1e-3)).astype(np.float32)
+    sm = (o["sigma"] - np.float32(1e-3)).astype(np.float32)
+    fdv, fdv_ref, noisev = fd_pair(o["S"], o["S"], sp, sm, sp, sm)
+    assert (np.abs(fdv - fdv_ref) <= noisev).all(), (np.abs(fdv - fdv_ref) / noisev).max()
+    vg = sig.grad.cpu().numpy().astype(np.float64) / wn
+    gapv = np.abs(rv - fdv_ref)
+    assert (np.abs(vg - fdv) <= gapv + noisev + 1e-5 * np.maximum(np.abs(rv), 1e-4 * Sn)).all()
+    kv = kinks(Sn, Sn, sm.astype(np.float64), sp.astype(np.float64))
+    # away from kinks the central quotient's truncation is O(h^2): small
+    assert (~kv).sum() >= 64 and (gapv[~kv] <= 1e-3 * np.maximum(np.abs(rv[~kv]), 1e-4 * Sn[~kv])).all()
 
 
 def test_no_grad_path_skips_greeks(A):
