@@ -55,10 +55,7 @@ SMALL = False  # --small: reduced sizes for profiler captures (never a bench val
 EXTRA_PROGRAMS = {"gemm_split6"}
 
 # ncu-measured DRAM bytes per launch of the dominant kernel (null once the kernel changes)
-NCU_TRAFFIC = {
-    "binomial": {"bytes_per_launch": 734.464e3 * 64,
-                 "source": "profiles/binomial_greeks_16384_options.md (16384 options x 64)"},
-}
+NCU_TRAFFIC = {}
 METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
 L2_FLUSH_BYTES = 512 << 20
 SMS_NOMINAL = 152
@@ -304,6 +301,7 @@ class Binomial(Workload):
         self.gws = self.n * 32
         st = self.o["steps"].astype(np.int64)
         self.nodes = int((st * (st + 1) // 2).sum())
+        self.nodes_price, self.nodes_adjoint = banded_node_updates(self.o)
 
     def setup(self):
         torch = self.torch
@@ -315,7 +313,8 @@ class Binomial(Workload):
         self.h_in = [t.pin_memory() for t in ts]
         self.h_out = [torch.zeros(self.n).pin_memory(), torch.zeros((self.n, 2)).pin_memory()]
         self.config = dict(options=self.n, steps="U{256..2048}", scheduler="hguided k=2 over 8 devices",
-                           outputs="price + delta + vega", node_updates=self.nodes)
+                           outputs="price + delta + vega", node_updates_full_lattice=self.nodes,
+                           node_updates_nonzero_band=self.nodes_price + self.nodes_adjoint)
 
     def program(self, ins, outs, greeks=True):
         S, K, T, sig, st = ins
@@ -378,11 +377,15 @@ class Binomial(Workload):
                     batched_over_plain=ms_batched / ms_plain)
 
     def after(self):
-        # FP32 instructions per node update: the price lattice and its adjoint
-        # (which gives delta and the vega leaf part) of 3 each (add, sub, FMA);
-        # flops with FMA = 2: 2 x 4
-        return dict(bound="alu", inst=6.0 * self.nodes, flops=8.0 * self.nodes, unit_name="options/s",
-                    units=self.n, extra={"node_updates_per_s": self.nodes})
+        # FP32 instructions per node update: 3 (add, sub, FMA; flops with
+        # FMA = 2: 4), over the nodes that can be nonzero: the backward
+        # induction's and its adjoint's (which gives delta and the vega leaf
+        # part) nonzero bands.  The full lattice's node count is reported
+        # beside it.
+        nb = self.nodes_price + self.nodes_adjoint
+        return dict(bound="alu", inst=3.0 * nb, flops=4.0 * nb, unit_name="options/s",
+                    units=self.n, extra={"node_updates_per_s": nb,
+                                         "full_lattice_node_updates_per_s": 2 * self.nodes})
 
     def cpu_sample(self, O, threads):
         t = time.perf_counter()
@@ -390,6 +393,29 @@ class Binomial(Workload):
         o = self.o
         O.binomial(o["S"][:k], o["K"][:k], o["T"][:k], o["sigma"][:k], o["steps"][:k], o["r"], threads=threads)
         return k / self.n, time.perf_counter() - t, "%d of %d options (price, delta, vega)" % (k, self.n)
+
+
+def banded_node_updates(o):
+    """Node updates of the binomial kernel's two passes over the nonzero band.
+
+    The out-of-the-money side is priced; its nonzero leaves form a run of b
+    leaves (FP64 estimate of the FP32 payoff test).  The backward induction
+    updates min(t + 1, b) nodes to produce level t (t = N-1 .. 0), the
+    adjoint min(t + 1, min(b, N)) weights at levels 1 .. N-1.
+    """
+    S, K, T, sig = (o[k].astype(np.float64) for k in ("S", "K", "T", "sigma"))
+    N = o["steps"].astype(np.int64)
+    a = sig * np.sqrt(T / N)
+    x = (N + np.log(K / S) / a) / 2.0           # leaf j is in the money for 2j - N vs ln(K/S)/a
+    put = S > K
+    b_put = np.clip(np.ceil(x), 0, N + 1)       # j < x
+    b_call = np.clip(N - np.floor(x), 0, N + 1)  # j > x
+    b = np.maximum(np.where(put, b_put, b_call), 1).astype(np.int64)
+    bb = np.minimum(b, N)
+    p0 = bb * (bb + 1) // 2 + (N - bb) * bb
+    nd = np.minimum(b, N)
+    p1 = nd * (nd + 1) // 2 - 1 + (N - nd) * nd
+    return int(p0.sum()), int(p1.sum())
 
 
 class Gemm(Workload):

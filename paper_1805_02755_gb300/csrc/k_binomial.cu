@@ -18,8 +18,10 @@
 // part 1/2 is exact and only the small q carries rounding.  The lattice is
 // stored scaled by 2 per level, B = 2^(N-t) V / disc^(N-t), so one node
 // update is  B_j <- (B_{j+1} + B_j) + 2q (B_{j+1} - B_j)  (add, sub, FMA);
-// every 32 levels all nodes are multiplied by 2^-32 (exact) and the power
-// is removed at the end together with disc^N = e^{-rT}.
+// the power of two is removed at the end together with disc^N = e^{-rT}.
+// Every 64 levels all nodes are multiplied by 2^-64 (exact); leaves stay
+// below ~1e16 (S = 100, sigma = 0.5, T = 2, N = 2048), so the scaled lattice
+// stays below ~2e35, inside the FP32 range.
 // In-the-money calls (S > K) are priced through the put on the same lattice
 // and put-call parity, which holds exactly on a CRR lattice:
 //   C = P + S - K e^{-rT},  dC/dS = dP/dS + 1,  dC/dsigma = dP/dsigma.
@@ -45,7 +47,19 @@
 //   vega = <A, vega leaves'> + N 2q' (B_1 - B_0).
 // Stored in reverse node order the adjoint recursion is the backward level
 // itself, so the price pass and the adjoint pass run on one copy of the
-// level code.  In FP32 emulation of this arithmetic against the FP64 oracle,
+// level code.
+// Only the out-of-the-money side is priced, so its nonzero leaves form one
+// contiguous run: j < b for the put, j > N - b for the call.  The call's
+// lattice is stored reflected (node j at index N - j), where its level is
+// the same operator with -2q in place of 2q (bit for bit: the difference
+// changes sign exactly, the sum commutes), so both sides have their
+// nonzero leaves at indices 0 .. b - 1.  Nodes at index >= b stay exactly
+// zero while the lattice is wider than b, so the backward induction runs at
+// the width that holds min(t + 1, b) nodes of level t, and the adjoint pass
+// stops widening once it holds the b weights the dot products use.  For the
+// near-the-money options of the workload b is about N / 2: a quarter of the
+// node updates of each pass are exact zeros that are never computed.
+// In FP32 emulation of this arithmetic against the FP64 oracle,
 // options of depth 1900..2048 show ~1.7e-6 relative error in the price,
 // ~0.9e-6 in delta and ~1.8e-6 in vega.
 #include <cuda_runtime.h>
@@ -66,13 +80,16 @@ struct BinoParams {
     int64_t n;
     float *price;
     float2 *greeks;  // (delta, vega) or nullptr
+    int full;        // 1: compute every node (the reference form of the banded lattice)
 };
 
 struct Lat {
-    float q2;      // 2q
+    float q2;      // 2q (-2q on the reflected lattice)
     int rescale;   // levels since the last rescale
     int shift;     // power of two still to remove from the result
 };
+
+constexpr int kRescale = 64;  // levels between rescales by 2^-64
 
 // Lane widths (nodes per lane) the warp steps through as the lattice shrinks.
 // Going from width R to the next width R' happens when the live nodes fit in
@@ -99,13 +116,15 @@ __device__ __forceinline__ int shidx(int j) { return j + (j >> 5); }  // avoids 
 
 // One level of the recursion B'_k = (B_k + B_{k+1}) + 2q (B_{k+1} - B_k) on
 // the first R slots of every lane (lane l holds nodes l*R .. l*R + R - 1).
-// The last lane's last slot takes node 0 as its upper neighbour (`src` =
-// lane + 1 mod 32): a dead slot in the backward induction, and in the
-// adjoint (stored reversed) node 0 is still zero whenever that slot is read.
+// The last lane's last slot takes zero as its upper neighbour: above the
+// top of the backward induction (a dead slot), above the nonzero band of a
+// lattice wider than the band (which keeps the nodes there at zero), and
+// the not-yet-reached node before node 0 in the adjoint (stored reversed).
 template <int R>
-__device__ __forceinline__ void level(float (&B)[kMaxR], float q2, int src)
+__device__ __forceinline__ void level(float (&B)[kMaxR], float q2, int src, bool top)
 {
-    const float bn = __shfl_sync(kFull, B[0], src);
+    float bn = __shfl_sync(kFull, B[0], src);
+    if (top) bn = 0.f;
 #pragma unroll
     for (int s = 0; s < R; ++s) {
         const float up = (s + 1 < R) ? B[s + 1] : bn;
@@ -133,18 +152,19 @@ __device__ __forceinline__ void levels(float (&B)[kMaxR], Lat &L, float *sh, int
 {
     constexpr int R = width_at(WI);
     const int src = (lane + 1) & (kWarp - 1);
-    // in runs up to the next rescale (every 32 levels, by 2^-32: exact)
+    const bool top = lane == kWarp - 1;
+    // in runs up to the next rescale (every kRescale levels, by 2^-kRescale: exact)
     while (n > 0) {
-        const int m = min(n, 32 - L.rescale);
+        const int m = min(n, kRescale - L.rescale);
 #pragma unroll 1
-        for (int i = 0; i < m; ++i) level<R>(B, L.q2, src);
+        for (int i = 0; i < m; ++i) level<R>(B, L.q2, src, top);
         n -= m;
         L.rescale += m;
-        if (L.rescale == 32) {
+        if (L.rescale == kRescale) {
             L.rescale = 0;
-            L.shift -= 32;
+            L.shift -= kRescale;
 #pragma unroll
-            for (int s = 0; s < R; ++s) B[s] *= 0x1p-32f;
+            for (int s = 0; s < R; ++s) B[s] *= 0x1p-64f;
         }
     }
     if (soff < 0) return;
@@ -196,16 +216,18 @@ __device__ __forceinline__ int width_for(int n)
 
 // Per-option constants of the lattice.
 struct Opt {
-    float S, K, sdt, a, q2;
+    float S, K, sdt, a, q2;  // q2: the level coefficient, -2q when reflected
     int N;
     bool put;
+    bool refl;  // the lattice is stored reflected (node j at index N - j)
 };
 
-// Leaf j (0..N) of the priced side: its payoff and, for the greeks, its
-// derivatives dS_T/dS (delta) and dS_T/dsigma (vega leaf part); all zero out
-// of the money.  One exp per leaf.
-__device__ __forceinline__ float leaf(const Opt &o, int j, float &dl, float &vg)
+// Leaf at index i (0..N) of the priced side: its payoff and, for the greeks,
+// its derivatives dS_T/dS (delta) and dS_T/dsigma (vega leaf part); all zero
+// out of the money.  One exp per leaf.
+__device__ __forceinline__ float leaf(const Opt &o, int i, float &dl, float &vg)
 {
+    const int j = o.refl ? o.N - i : i;
     const float m = (float)(2 * j - o.N);
     const float g = expf(o.a * m);
     const float ST = o.S * g;
@@ -220,40 +242,53 @@ __device__ __forceinline__ float leaf(const Opt &o, int j, float &dl, float &vg)
 }
 
 // The payoffs of leaves 0..N into the warp's shared buffer, zero beyond N.
-__device__ __forceinline__ void leaves(const Opt &o, float *sh, int lane)
+// Returns b, one past the last nonzero leaf (at least 1).
+__device__ __forceinline__ int leaves(const Opt &o, float *sh, int lane)
 {
     __syncwarp();
+    int last = 0;
     for (int j = lane; j <= kMaxSteps; j += kWarp) {
         float dl, vg;
-        sh[shidx(j)] = (j <= o.N) ? leaf(o, j, dl, vg) : 0.f;
+        const float v = (j <= o.N) ? leaf(o, j, dl, vg) : 0.f;
+        sh[shidx(j)] = v;
+        if (v != 0.f) last = j;
     }
     __syncwarp();
+    return __reduce_max_sync(kFull, last) + 1;
 }
 
 // The lattice passes of one option over the leaves in shared buffer 0,
 // which each pass then uses as its repack buffer.
 //
 // Pass 0, the backward induction: from the N + 1 leaves (level N) down to
-// the root.  The widths are walked downwards: at width R the levels run until
-// the live nodes fit the next width, then the nodes are repacked through the
-// shared buffer.  Gives the root on lane 0 (scaled by 2^shift) and, on lane
-// 0, d1 = B_1 - B_0 of level 1 at the root's scaling.
+// the root.  The widths are walked downwards, starting at the width that
+// holds min(N + 1, b) nodes (nodes from b up are zero): at width R the levels
+// run until the level's nodes fit the next width, then the nodes are
+// repacked through the shared buffer.  Gives the root on lane 0 (scaled by
+// 2^shift) and, on lane 0, d1 = B_1 - B_0 of level 1 (stored order) at the
+// root's scaling.
 //
 // Pass 1 (greeks), its adjoint: weights A on the nodes of level N - 1 with
 // root = sum_j A_j x_j for any level N - 1 of this recursion.  From the root
 // (A = 1) outwards A'_j = (A_j + A_{j-1}) + 2q (A_{j-1} - A_j), one node more
 // per level.  Stored reversed (node j at slot 32R - 1 - j) this is the
 // backward level itself, with the slots not reached yet at zero, so it runs
-// on the same code while the widths are walked upwards.  Leaves node j of
-// level N - 1 at shared node 32 Rf - 1 - j (Rf returned in `rf`), with the
+// on the same code while the widths are walked upwards, until the width
+// holds the min(b, N) weights the dot products use (a node's weight depends
+// only on nodes of lower index, so the rest of the level can be left out).
+// Leaves node j < min(b, N) of level N - 1 at shared node 32 Rf - 1 - j
+// (Rf returned in `rf`), with the
 // power of two in A in shift_a: N - 1 levels here, and the one that pushes
 // the leaves back to level N - 1, applied by the caller, counted too.
 //
 // Both passes go through one call of levels_at and one of load_width_at, so
 // each width's code exists once in the kernel: the instruction footprint,
 // not the arithmetic, limits the deep lattices.
-__device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, bool adj, int &shift, float &d1,
-                                         int &shift_a, int &rf)
+//
+// The lattice is a call of its own (not inlined): its register allocation
+// is then independent of the caller's, which measured 5% faster.
+__device__ __noinline__ float lattice(const Opt &o, int band, float *sh, int lane, bool adj, int &shift,
+                                      float &d1, int &shift_a, int &rf)
 {
     Lat L;
     L.q2 = o.q2;
@@ -266,9 +301,9 @@ __device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, bool
         int wi, active, lo = 0;
         bool load = false, captured = false;
         if (pass == 0) {
-            if (o.N + 1 <= kMaxSteps) {
-                // the N + 1 leaves as level N, at the narrowest width that holds them
-                wi = width_for<0>(o.N + 1);
+            if (min(o.N + 1, band) <= kMaxSteps) {
+                // level N at the narrowest width that holds its nonzero band
+                wi = width_for<0>(min(o.N + 1, band));
                 load = true;
                 active = o.N + 1;
             } else {
@@ -311,11 +346,11 @@ __device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, bool
                     fin = true;
                 }
             } else {
-                const int cap = min(kWarp * R, o.N);
-                n = cap - active;
-                if (cap == o.N) {
+                if (kWarp * R >= min(band, o.N)) {  // holds the weights used: the rest at this width
+                    n = o.N - active;
                     fin = true;
                 } else {
+                    n = kWarp * R - active;
                     next = wi - 1;
                     soff = kWarp * (width_rt<0>(next) - R);
                     load = true;
@@ -332,7 +367,7 @@ __device__ __forceinline__ float lattice(const Opt &o, float *sh, int lane, bool
             wi = next;
         }
         if (pass == 0) {
-            if (L.rescale == 0) d1 *= 0x1p-32f;
+            if (L.rescale == 0) d1 *= 0x1p-64f;
             shift = L.shift;
             root = B[0];
         } else {
@@ -368,17 +403,20 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     op.K = K;
     op.sdt = sdt;
     op.a = a;
-    op.q2 = 2.0f * q;
     op.N = N;
     op.put = S > K;  // price the out-of-the-money side, then parity
+    op.refl = !op.put && !p.full;  // the call's nonzero leaves are the high ones: reflect
+    op.q2 = op.refl ? -2.0f * q : 2.0f * q;
     // price by backward induction; with greeks one adjoint pass gives delta
     // and the vega leaf part as dot products of its weights with the leaves
     const bool greeks = G && p.greeks;
     int shift = 0;
     float d1 = 0.f;
     int shift_a = 0, rf = 0;
-    leaves(op, sh, lane);
-    const float b = lattice(op, sh, lane, greeks, shift, d1, shift_a, rf);
+    const int nz = leaves(op, sh, lane);
+    const int band = p.full ? N + 1 : nz;
+    const float b = lattice(op, band, sh, lane, greeks, shift, d1, shift_a, rf);
+    if (op.refl) d1 = -d1;  // B_1 - B_0 in node order
     float delta = 0.f, vega = 0.f;
     if (greeks) {
         const int top = kWarp * rf - 1;  // node j of level N - 1 at shared node top - j
@@ -386,7 +424,8 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
         // dotted with A; the leaves are evaluated again here rather than kept
         // in shared memory (two buffers would halve the resident warps)
         float sd = 0.f, sv = 0.f;
-        for (int j = lane; j < N; j += kWarp) {
+        const int need = min(band, N);  // the pushed-back leaf derivatives are zero from there on
+        for (int j = lane; j < need; j += kWarp) {
             const float w = sh[shidx(top - j)];
             float d0, v0, d1l, v1;
             leaf(op, j, d0, v0);
@@ -499,6 +538,7 @@ struct BinoBatchBody {
         bp.n = in.n;
         bp.price = in.price;
         bp.greeks = G ? in.greeks : nullptr;
+        bp.full = 0;
         price_option<G>(bp, local, sh);
     }
 };
@@ -560,6 +600,7 @@ uint32_t nchunks(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { re
 
 int ctas_per_sm() { return occ((const void *)k_binomial<true>); }
 
+template <bool FULL>
 ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
     BinoParams p;
@@ -572,6 +613,7 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.n = a.i32(6);
     p.price = a.buf<float>(7);
     p.greeks = a.buf<float2>(8);
+    p.full = FULL ? 1 : 0;
     if (p.greeks)
         k_binomial<true><<<c.grid, kWarp, 0, c.stream>>>(p, s);
     else
@@ -639,7 +681,18 @@ extern const KernelDesc kBinomial = {
     "binomial", 9,
     {{"S", A_BUF_IN}, {"K", A_BUF_IN}, {"T", A_BUF_IN}, {"sigma", A_BUF_IN}, {"steps", A_BUF_IN},
      {"r", A_F32}, {"n", A_I32}, {"price", A_BUF_OUT}, {"greeks", A_BUF_OUT_OPT}},
-    1, 0, kWarp, 0, validate, grain, nchunks, ctas_per_sm, launch,
+    1, 0, kWarp, 0, validate, grain, nchunks, ctas_per_sm, launch<false>,
+};
+
+// The same program computing every node of every level, without the
+// reflection of the call lattice: the reference form of the banded lattice
+// (identical prices, and greeks up to the summation order of the calls' dot
+// products).
+extern const KernelDesc kBinomialFull = {
+    "binomial_full", 9,
+    {{"S", A_BUF_IN}, {"K", A_BUF_IN}, {"T", A_BUF_IN}, {"sigma", A_BUF_IN}, {"steps", A_BUF_IN},
+     {"r", A_F32}, {"n", A_I32}, {"price", A_BUF_OUT}, {"greeks", A_BUF_OUT_OPT}},
+    1, 0, kWarp, 0, validate, grain, nchunks, ctas_per_sm, launch<true>,
 };
 
 }  // namespace ecl

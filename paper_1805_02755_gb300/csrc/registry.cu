@@ -15,6 +15,7 @@ extern const KernelDesc kNBodyEnergy;
 extern const KernelDesc kNBodyFD;
 extern const KernelDesc kBinomial;
 extern const KernelDesc kBinomialBatch;
+extern const KernelDesc kBinomialFull;
 extern const KernelDesc kGemmBF16;
 extern const KernelDesc kGemmSplit3;
 extern const KernelDesc kGemmSplit6;
@@ -32,6 +33,7 @@ static const KernelDesc *const kAll[] = {
     &kNBodyFD,
     &kBinomial,
     &kBinomialBatch,
+    &kBinomialFull,
     &kGemmBF16,
     &kGemmSplit3,
     &kGemmSplit6,

@@ -11,7 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-KERNELS = ["mandelbrot", "gaussian", "nbody", "nbody_acc", "nbody_adjoint", "nbody_energy", "nbody_fd", "binomial", "binomial_batch", "gemm_bf16", "gemm_split3", "gemm_split6", "cast_bf16", "ray", "fp32_probe"]
+KERNELS = ["mandelbrot", "gaussian", "nbody", "nbody_acc", "nbody_adjoint", "nbody_energy", "nbody_fd", "binomial", "binomial_batch", "binomial_full", "gemm_bf16", "gemm_split3", "gemm_split6", "cast_bf16", "ray", "fp32_probe"]
 
 
 @pytest.fixture(scope="module")
@@ -131,3 +131,31 @@ def test_table2_binomial_differs_as_documented(E):
     writes = sum(1 for k, _ in args if k in (E.ECL_ARG_BUF_OUT, E.ECL_ARG_BUF_OUT_OPT))
     assert (len(args), reads, writes) == (9, 5, 2)
     assert (len(args), reads, writes) != (want["args"], want["reads"], want["writes"])
+
+
+@pytest.mark.parametrize("case", ["pos_dtype", "pos_short", "pos_strided", "pos_numpy", "out_dtype", "out_empty",
+                                  "on_host"])
+def test_noalloc_energy_wrapper_rejects_bad_tensors(E, case):
+    # The no-allocation energy call hands bare addresses to C, which cannot
+    # see sizes: the binding checks dtype, contiguity, size and device before
+    # any CUDA call (these run on the CPU and never reach the library).
+    import numpy as np
+    import torch
+    n = 8
+    pos = torch.zeros((n, 4), dtype=torch.float32)
+    out = torch.zeros(1, dtype=torch.float64)
+    msg = "current CUDA device"
+    if case == "pos_dtype":
+        pos, msg = pos.double(), "pos4 must be torch.float32"
+    elif case == "pos_short":
+        pos, msg = torch.zeros((n - 1, 4)), "pos4 holds 28 values, 32 needed"
+    elif case == "pos_strided":
+        pos, msg = torch.zeros((n, 8))[:, :4], "pos4 must be contiguous"
+    elif case == "pos_numpy":
+        pos, msg = np.zeros((n, 4), np.float32), "pos4 must be a torch tensor"
+    elif case == "out_dtype":
+        out, msg = out.float(), "out_energy must be torch.float64"
+    elif case == "out_empty":
+        out, msg = torch.zeros(0, dtype=torch.float64), "out_energy holds 0 values, 1 needed"
+    with pytest.raises(ValueError, match=msg):
+        E.ecl_nbody_energy_noalloc(pos, n, 1e-3, out)

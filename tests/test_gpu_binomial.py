@@ -25,7 +25,7 @@ def E():
     return E
 
 
-def run_bino(E, o, greeks=True, sched="hguided", params=(2.0, 1.0), D=8, C=0, coverage=False):
+def run_bino(E, o, greeks=True, sched="hguided", params=(2.0, 1.0), D=8, C=0, coverage=False, kernel="binomial"):
     import torch
     n = len(o["S"])
     t = {k: torch.from_numpy(np.ascontiguousarray(o[k])).cuda() for k in ("S", "K", "T", "sigma", "steps")}
@@ -33,7 +33,7 @@ def run_bino(E, o, greeks=True, sched="hguided", params=(2.0, 1.0), D=8, C=0, co
     gr = torch.full((n, 2), -1.0, device="cuda") if greeks else None
     eng = E.Engine(0)
     cov = torch.zeros(n, dtype=torch.int32, device="cuda") if coverage else None
-    p = E.Program("binomial")
+    p = E.Program(kernel)
     for k in ("S", "K", "T", "sigma", "steps"):
         p.in_(t[k])
     p.out(price)
@@ -109,3 +109,35 @@ def test_config4_full_batch_sampled(E, oracle_mod):
     lb = np.maximum(S - K * np.exp(-o["r"] * T), 0)
     assert (price >= lb - 1e-4 * S).all() and (price <= S * (1 + 1e-6)).all()
     assert (gr[:, 0] >= -1e-6).all() and (gr[:, 0] <= 1 + 1e-5).all() and (gr[:, 1] >= -1e-4).all()
+
+
+def test_banded_lattice_matches_the_full_lattice(E):
+    # The banded program skips nodes that are exactly zero and stores the
+    # call lattice reflected; the full program computes every node in node
+    # order.  Prices agree bit for bit; greeks agree bit for bit for the puts
+    # (in-the-money calls) and up to the summation order of the dot products
+    # for the calls.  Every width boundary, the extremes, then a random batch.
+    widths = [1, 2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64]
+    steps = sorted({v for w in widths for v in (32 * w - 1, 32 * w, 32 * w + 1) if 1 <= v <= 2048} | {1, 2, 3})
+    o = W.binomial_options(len(steps), seed=44)
+    o["steps"] = np.array(steps, dtype=np.int32)
+    for opts in (o, W.binomial_options(4096, seed=45)):
+        for greeks in (True, False):
+            pb, gb, _ = run_bino(E, opts, greeks, kernel="binomial")
+            pf, gf, _ = run_bino(E, opts, greeks, kernel="binomial_full")
+            assert np.array_equal(pb.view(np.uint32), pf.view(np.uint32))
+            if greeks:
+                put = opts["S"] > opts["K"]
+                assert np.array_equal(gb[put].view(np.uint32), gf[put].view(np.uint32))
+                scale = np.maximum(np.abs(gf), np.array([1e-4, 1e-4]) * opts["S"][:, None])
+                assert (np.abs(gb - gf) <= 1e-6 * scale).all()
+
+
+def test_deep_out_of_the_money_band_of_one_leaf(E, oracle_mod):
+    # strikes far from the spot: no leaf or a single leaf in the money
+    o = W.binomial_options(64, seed=46, min_steps=1, max_steps=2048)
+    o["K"] = (o["S"] * np.where(np.arange(64) % 2 == 0, 40.0, 0.02)).astype(np.float32)
+    price, gr, _ = run_bino(E, o)
+    pf, gf, _ = run_bino(E, o, kernel="binomial_full")
+    assert np.array_equal(price.view(np.uint32), pf.view(np.uint32))
+    check(o, price, gr, oracle_mod)
