@@ -121,6 +121,27 @@ typedef struct ecl_binomial_instance {
     int32_t pad;
 } ecl_binomial_instance;
 
+/* One view of "mandelbrot_batch" (56 bytes, the layout of the device table). */
+typedef struct ecl_mandelbrot_view {
+    uint32_t *out;                  /* device uint32[W*H], 16-byte aligned */
+    int32_t W, H;                   /* pixels */
+    float x0, y0, dx, dy;           /* pixel (i, j) -> c = (x0 + i dx, y0 + j dy) */
+    int32_t max_iter;
+    int32_t pad;
+    int64_t first;                  /* first work-group of this view in the NDRange */
+    int64_t wgs;                    /* its work-groups: ceil(W*H / 4 / 256) */
+} ecl_mandelbrot_view;
+
+/* One image of "gaussian_batch" (48 bytes, the layout of the device table). */
+typedef struct ecl_gaussian_image {
+    const float *in;                /* device float[W*H] row-major */
+    float *out;                     /* device float[W*H], 16-byte aligned */
+    const float *w;                 /* device float[31] filter weights */
+    int32_t W, H;
+    int64_t first;                  /* first work-group (tile) of this image in the NDRange */
+    int64_t tiles;                  /* its tiles: ceil(H/32) * ceil(W/224) */
+} ecl_gaussian_image;
+
 /* ---------------------------------------------------------------- engine */
 
 /* Creates an engine on CUDA device `device_ordinal` (Sec. 6 and Listing 1:
@@ -377,7 +398,12 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   European call on a Cox-Ross-Rubinstein lattice of steps[o] steps,
  *   backward induction in FP32 by one warp per option; with greeks the
  *   exact derivatives of the lattice price with respect to S and sigma
- *   (forward mode through the same lattice).
+ *   (one adjoint pass of the lattice).  Nodes that are exactly zero (below
+ *   the strike on the out-of-the-money side) are not computed.
+ *
+ * "binomial_full"  (the arguments of "binomial")  the same prices computing
+ *   every node of every level: the reference form of "binomial" (identical
+ *   prices; greeks equal up to the summation order of their dot products).
  *
  * "binomial_batch"  (4 args, out pattern 1:32, lws 32)  many option batches
  *   of uneven size in one NDRange and one persistent launch:
@@ -387,6 +413,27 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   ascending from 0, sum of n_i = total) from its own arrays; with_greeks = 0
  *   skips the delta/vega lattices for the whole batch.  The engine does not
  *   see the arrays the table points to: the caller guarantees them.
+ *
+ * "mandelbrot_batch"  (3 args, one output pixel block per work-item, lws
+ *   256)  many views of uneven size in one NDRange and one persistent launch
+ *   (not in the paper: its package model over a concatenated NDRange):
+ *     0 B views ecl_mandelbrot_view[count] (device, 16-byte aligned)
+ *     1 S int32 count  2 S int64 total work-groups
+ *   view i owns work-groups [first_i, first_i + wgs_i) (first ascending from
+ *   0) and computes them as "mandelbrot" does its own.  A view with a
+ *   misaligned output or no pixels is skipped.  The engine does not see the
+ *   arrays the table points to: the caller guarantees them.
+ *
+ * "gaussian_batch"  (3 args, lws 256 = one 32 x 224 output tile per
+ *   work-group)  many images of uneven size, 31 taps each with their own
+ *   weights, clamp-to-edge, in one NDRange and one persistent launch (not in
+ *   the paper: its package model over a concatenated NDRange of tiles):
+ *     0 B images ecl_gaussian_image[count] (device, 16-byte aligned)
+ *     1 S int32 count  2 S int64 total tiles
+ *   image i owns work-groups [first_i, first_i + tiles_i), tile t at rows
+ *   32 (t / ceil(W/224)), columns 224 (t % ceil(W/224)).  An image with a
+ *   misaligned output or no pixels is skipped.  The caller guarantees the
+ *   arrays the table points to.
  *
  * "gemm_bf16"  (6 args; lws 32768 = one 128 x 256 output tile; the
  *   scheduling unit is one row of tiles)

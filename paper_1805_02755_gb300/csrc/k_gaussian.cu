@@ -196,9 +196,11 @@ struct Gauss31Body {
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     }
 
-    __device__ __forceinline__ void run(uint64_t off, uint64_t len, uint32_t t, uint32_t)
+    __device__ __forceinline__ void run(uint64_t off, uint64_t len, uint32_t t, uint32_t) { tile(geom(p, off, len, t)); }
+
+    // One 32-row x 224-column output tile of the image p.
+    __device__ __forceinline__ void tile(const ChunkGeom &g)
     {
-        const ChunkGeom g = geom(p, off, len, t);
         stage(g);
         body_sync(kBlock);
         // vertical pass: staged column c <-> image column x0 - 16 + c, one column per thread
@@ -269,6 +271,86 @@ __global__ void __launch_bounds__(kBlock + 32, 3) k_gauss31(GaussParams prm, Sch
     b.st = reinterpret_cast<float(*)[kSW]>(smem_g);
 #pragma unroll
     for (int u = 0; u < 31; ++u) b.wr[u] = __ldg(prm.w + u);
+    drive_ws(s, b);
+}
+
+// ---------------------------------------------------------------- batches
+// Many images of uneven size (31 taps each, own weights) as one NDRange of
+// tiles: image i owns work-groups [first_i, first_i + tiles_i), one per
+// 32-row x 224-column output tile (row-major over the image's tile grid);
+// a work-group finds its image by binary search over `first`.  Mirrors
+// ecl_gaussian_image in include/ecl.h.
+struct GaussImage {
+    const float *in;
+    float *out;
+    const float *w;
+    int32_t W, H;
+    int64_t first;
+    int64_t tiles;
+};
+static_assert(sizeof(GaussImage) == 48, "ecl_gaussian_image layout");
+
+__host__ __device__ inline int64_t gauss_tiles(int64_t W, int64_t H)
+{
+    return ((H + kRB - 1) / kRB) * ((W + kTW - 1) / kTW);
+}
+
+struct GaussBatchParams {
+    const GaussImage *img;
+    int32_t count;
+    int64_t total;
+};
+
+struct Gauss31BatchBody {
+    static constexpr uint32_t kThreads = kBlock;
+    using Params = GaussBatchParams;
+    Params p;
+    Gauss31Body b;
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const int64_t wg = (int64_t)(off + t);
+        if (wg >= p.total) return;
+        int lo = 0, hi = p.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&p.img[mid].first) <= wg) lo = mid;
+            else hi = mid - 1;
+        }
+        const GaussImage &im = p.img[lo];
+        const int64_t local = wg - im.first;
+        // out of range, empty, or an output the 128-bit stores cannot use: skipped
+        if (local < 0 || local >= im.tiles || im.W <= 0 || im.H <= 0 || ((uintptr_t)im.out & 15) ||
+            local >= gauss_tiles(im.W, im.H))
+            return;
+        b.p.in = im.in;
+        b.p.out = im.out;
+        b.p.w = im.w;
+        b.p.W = im.W;
+        b.p.H = im.H;
+        b.p.taps = 31;
+        b.p.lws = 1;
+#pragma unroll
+        for (int u = 0; u < 31; ++u) b.wr[u] = __ldg(im.w + u);
+        const int64_t ntx = (im.W + kTW - 1) / kTW;
+        ChunkGeom g;
+        g.p0 = 0;
+        g.p1 = (int64_t)im.W * im.H;
+        g.y0 = (local / ntx) * kRB;
+        g.rows = min((int64_t)kRB, (int64_t)im.H - g.y0);
+        g.x0 = (local % ntx) * kTW;
+        b.tile(g);
+    }
+};
+
+__global__ void __launch_bounds__(kBlock + 32, 3) k_gauss31_batch(GaussBatchParams prm, SchedArgs s)
+{
+    extern __shared__ __align__(16) float smem_g[];
+    Gauss31BatchBody b;
+    b.p = prm;
+    b.b.st = reinterpret_cast<float(*)[kSW]>(smem_g);
     drive_ws(s, b);
 }
 
@@ -377,7 +459,73 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     return ECL_OK;
 }
 
+// ---- gaussian_batch: table of images, count, total tiles
+ecl_status v_batch(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    const int64_t count = a.i32(1), total = a.i64(2);
+    if (count <= 0 || total <= 0) {
+        err = "count and total must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (a.bytes[0] < (uint64_t)count * sizeof(GaussImage) || (uintptr_t)a.ptr[0] % 16) {
+        err = "the image table must hold count 16-byte aligned entries of 48 bytes";
+        return ECL_ERR_BUFFER;
+    }
+    if (lws != kBlock) {
+        err = "lws must be 256 (one work-group per output tile)";
+        return ECL_ERR_SIZE;
+    }
+    if (gws < (uint64_t)total * kBlock) {
+        err = "the NDRange does not cover the images' tiles";
+        return ECL_ERR_SIZE;
+    }
+    return ECL_OK;
+}
+
+uint32_t nchunks_batch(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+bool set_smem_attr_batch()
+{
+    static std::atomic<unsigned long long> done{0};
+    return smem_limit_once((const void *)k_gauss31_batch, (int)kSmem31, done);
+}
+
+int batch_ctas_per_sm()
+{
+    if (!set_smem_attr_batch()) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gauss31_batch, kBlock + 32, kSmem31) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    if (!set_smem_attr_batch()) {
+        err = "cannot raise the shared-memory limit";
+        return ECL_ERR_CUDA;
+    }
+    GaussBatchParams p;
+    p.img = a.buf<const GaussImage>(0);
+    p.count = a.i32(1);
+    p.total = a.i64(2);
+    k_gauss31_batch<<<c.grid, kBlock + 32, kSmem31, c.stream>>>(p, s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
+}
+
 }  // namespace
+
+extern const KernelDesc kGaussianBatch = {
+    "gaussian_batch", 3, {{"images", A_BUF_IN}, {"count", A_I32}, {"total", A_I64}},
+    1, 0, kBlock + 32, 0, v_batch, grain, nchunks_batch, batch_ctas_per_sm, l_batch,
+};
 
 extern const KernelDesc kGaussian = {
     "gaussian",

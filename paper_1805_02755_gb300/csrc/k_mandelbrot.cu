@@ -37,10 +37,12 @@ struct MandelbrotBody {
         return (uint32_t)len;
     }
 
-    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t) { workgroup(p, off + t); }
+
+    // Work-group wg of the view p: its lws work-items, 4 pixels each.
+    static __device__ __forceinline__ void workgroup(const Params &p, uint64_t wg)
     {
         const uint64_t npx = (uint64_t)p.W * (uint64_t)p.H;
-        const uint64_t wg = off + t;
         const uint64_t wi_end = (wg + 1) * p.lws;
         for (uint64_t wi = wg * p.lws + threadIdx.x; wi < wi_end; wi += kBlock) {
             const uint64_t px0 = wi * 4;
@@ -89,6 +91,67 @@ struct MandelbrotBody {
 __global__ void __launch_bounds__(kBlock + 32) k_mandelbrot(MandelbrotBody::Params prm, SchedArgs s)
 {
     MandelbrotBody b{prm};
+    drive_ws(s, b);
+}
+
+// ---------------------------------------------------------------- batches
+// Many views of uneven size as one NDRange: view i owns work-groups
+// [first_i, first_i + wgs_i) of lws 256; a work-group finds its view by
+// binary search over `first` (ascending, first_0 = 0).  Mirrors
+// ecl_mandelbrot_view in include/ecl.h.
+struct MandelView {
+    uint32_t *out;
+    int32_t W, H;
+    float x0, y0, dx, dy;
+    int32_t max_iter;
+    int32_t pad;
+    int64_t first;
+    int64_t wgs;
+};
+static_assert(sizeof(MandelView) == 56, "ecl_mandelbrot_view layout");
+
+struct MandelBatchBody {
+    static constexpr uint32_t kThreads = kBlock;
+    struct Params {
+        const MandelView *views;
+        int32_t count;
+        int64_t total;
+    };
+    Params p;
+
+    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+    __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
+    {
+        const int64_t wg = (int64_t)(off + t);
+        if (wg >= p.total) return;
+        int lo = 0, hi = p.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&p.views[mid].first) <= wg) lo = mid;
+            else hi = mid - 1;
+        }
+        const MandelView &v = p.views[lo];
+        const int64_t local = wg - v.first;
+        // out of range, empty, or an output the 128-bit stores cannot use: skipped
+        if (local < 0 || local >= v.wgs || v.W <= 0 || v.H <= 0 || ((uintptr_t)v.out & 15)) return;
+        MandelbrotBody::Params q;
+        q.out = v.out;
+        q.W = v.W;
+        q.H = v.H;
+        q.x0 = v.x0;
+        q.y0 = v.y0;
+        q.dx = v.dx;
+        q.dy = v.dy;
+        q.max_iter = v.max_iter;
+        q.lws = kBlock;
+        MandelbrotBody::workgroup(q, (uint64_t)local);
+    }
+};
+
+__global__ void __launch_bounds__(kBlock + 32) k_mandelbrot_batch(MandelBatchBody::Params prm, SchedArgs s)
+{
+    MandelBatchBody b{prm};
     drive_ws(s, b);
 }
 
@@ -166,7 +229,62 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     return ECL_OK;
 }
 
+// ---- mandelbrot_batch: table of views, count, total work-groups
+ecl_status v_batch(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
+{
+    const int64_t count = a.i32(1), total = a.i64(2);
+    if (count <= 0 || total <= 0) {
+        err = "count and total must be positive";
+        return ECL_ERR_ARG;
+    }
+    if (a.bytes[0] < (uint64_t)count * sizeof(MandelView) || (uintptr_t)a.ptr[0] % 16) {
+        err = "the view table must hold count 16-byte aligned entries of 56 bytes";
+        return ECL_ERR_BUFFER;
+    }
+    if (lws != kBlock) {
+        err = "lws must be 256";
+        return ECL_ERR_SIZE;
+    }
+    if (gws < (uint64_t)total * kBlock) {
+        err = "the NDRange does not cover the views' work-groups";
+        return ECL_ERR_SIZE;
+    }
+    return ECL_OK;
+}
+
+uint32_t nchunks_batch(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
+
+int batch_ctas_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mandelbrot_batch, kBlock + 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
+{
+    MandelBatchBody::Params p;
+    p.views = a.buf<const MandelView>(0);
+    p.count = a.i32(1);
+    p.total = a.i64(2);
+    k_mandelbrot_batch<<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("launch: ") + cudaGetErrorString(ce);
+        return ECL_ERR_CUDA;
+    }
+    return ECL_OK;
+}
+
 }  // namespace
+
+extern const KernelDesc kMandelbrotBatch = {
+    "mandelbrot_batch", 3, {{"views", A_BUF_IN}, {"count", A_I32}, {"total", A_I64}},
+    1, 0, kBlock + 32, 0, v_batch, grain, nchunks_batch, batch_ctas_per_sm, l_batch,
+};
 
 extern const KernelDesc kMandelbrot = {
     "mandelbrot",

@@ -8,6 +8,8 @@ namespace ecl {
 
 extern const KernelDesc kMandelbrot;
 extern const KernelDesc kGaussian;
+extern const KernelDesc kGaussianBatch;
+extern const KernelDesc kMandelbrotBatch;
 extern const KernelDesc kNBody;
 extern const KernelDesc kNBodyAcc;
 extern const KernelDesc kNBodyAdjoint;
@@ -26,6 +28,8 @@ extern const KernelDesc kFp32Probe;
 static const KernelDesc *const kAll[] = {
     &kMandelbrot,
     &kGaussian,
+    &kGaussianBatch,
+    &kMandelbrotBatch,
     &kNBody,
     &kNBodyAcc,
     &kNBodyAdjoint,

@@ -11,7 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-KERNELS = ["mandelbrot", "gaussian", "nbody", "nbody_acc", "nbody_adjoint", "nbody_energy", "nbody_fd", "binomial", "binomial_batch", "binomial_full", "gemm_bf16", "gemm_split3", "gemm_split6", "cast_bf16", "ray", "fp32_probe"]
+KERNELS = ["mandelbrot", "gaussian", "gaussian_batch", "mandelbrot_batch", "nbody", "nbody_acc", "nbody_adjoint", "nbody_energy", "nbody_fd", "binomial", "binomial_batch", "binomial_full", "gemm_bf16", "gemm_split3", "gemm_split6", "cast_bf16", "ray", "fp32_probe"]
 
 
 @pytest.fixture(scope="module")

@@ -112,3 +112,130 @@ def test_autotune_picks_and_caches(E, tmp_path):
     assert res["config"] in space and len(res["table"]) == 3 and res["ms"] > 0
     again = autotune.autotune("mandelbrot", prog, Wd * H // 4, 256, space=[], cache_path=cache)
     assert again["config"] == res["config"]
+
+
+# ---------------------------------------------------------------- many views / images
+VIEWS = [  # (W, H, x0, y0, dx, dy, max_iter): uneven sizes, ragged work-groups, zooms
+    (1024, 768, -2.0, -1.5, 3.0 / 1024, 3.0 / 768, 256),
+    (37, 5, -0.75, 0.05, 0.003, 0.002, 100),
+    (1, 1, -0.5, 0.0, 0.01, 0.01, 64),
+    (333, 129, -0.7453, 0.1127, 6.5e-5, 6.5e-5, 500),
+    (64, 64, -1.8, -0.1, 0.003, 0.003, 1),
+    (2000, 3, -2.0, -0.01, 0.0015, 0.01, 300),
+]
+
+
+def make_views(torch):
+    out = []
+    for (Wd, H, x0, y0, dx, dy, it) in VIEWS:
+        out.append(dict(out=torch.full((Wd * H,), -1, dtype=torch.int32, device="cuda"), W=Wd, H=H,
+                        x0=np.float32(x0), y0=np.float32(y0), dx=np.float32(dx), dy=np.float32(dy), max_iter=it))
+    return out
+
+
+def check_views(views, oracle_mod):
+    for v in views:
+        ref = oracle_mod.mandelbrot(v["W"], v["H"], v["x0"], v["y0"], v["dx"], v["dy"], v["max_iter"])
+        got = v["out"].cpu().numpy().view(np.uint32).reshape(v["H"], v["W"])
+        assert np.array_equal(got, ref), (v["W"], v["H"])
+
+
+@pytest.mark.parametrize("sched,params,D,C", [("hguided", (2.0, 1.0), 0, 0), ("dynamic", (16,), 8, 0),
+                                              ("static", (), 1, 0), ("hguided", (1.0, 4.0), 4, 3)])
+def test_mandelbrot_views_one_launch_bit_exact(E, oracle_mod, sched, params, D, C):
+    import torch
+    from paper_1805_02755_gb300.batching import MandelbrotBatch
+    views = make_views(torch)
+    mb = MandelbrotBatch(views, scheduler=(sched, params), workers=(D, C))
+    cov = torch.zeros(mb.total, dtype=torch.int32, device="cuda")
+    mb.engine.set_coverage(cov)
+    mb.run().engine.synchronize()
+    assert mb.engine.plan_info()["G"] == sum(MandelbrotBatch.workgroups(v[0], v[1]) for v in VIEWS)
+    assert (cov.cpu().numpy() == 1).all()  # every work-group of every view exactly once
+    check_views(views, oracle_mod)
+    mb.close()
+
+
+IMAGES = [(96, 160, 5.0), (33, 300, 2.0), (512, 17, 8.0), (1, 1, 5.0), (250, 700, 3.5), (40, 225, 5.0)]  # H, W, sigma
+
+
+def make_images(torch):
+    out = []
+    for i, (H, Wd, sg) in enumerate(IMAGES):
+        img = W.gaussian_image(H, Wd, seed=900 + i)
+        w = W.gaussian_weights(31, sg)
+        out.append(dict(host=img, hw=w, **{"in": torch.from_numpy(img).cuda()},
+                        out=torch.full((H * Wd,), -1.0, device="cuda"), w=torch.from_numpy(w).cuda(), W=Wd, H=H))
+    return out
+
+
+def check_images(images, oracle_mod):
+    for im in images:
+        ref = oracle_mod.gaussian(im["host"], im["hw"])
+        got = im["out"].cpu().numpy().reshape(im["H"], im["W"])
+        assert (np.abs(got - ref) <= 1e-5 * np.abs(ref)).all(), (im["H"], im["W"])
+
+
+@pytest.mark.parametrize("sched,params,D,C", [("hguided", (2.0, 1.0), 0, 0), ("dynamic", (7,), 0, 0),
+                                              ("static", (0.3, 0.3), 3, 0)])
+def test_gaussian_images_one_launch(E, oracle_mod, sched, params, D, C):
+    import torch
+    from paper_1805_02755_gb300.batching import GaussianBatch
+    images = make_images(torch)
+    gb = GaussianBatch(images, scheduler=(sched, params), workers=(D, C))
+    cov = torch.zeros(gb.total, dtype=torch.int32, device="cuda")
+    gb.engine.set_coverage(cov)
+    gb.run().engine.synchronize()
+    assert gb.total == sum(GaussianBatch.tiles(w, h) for (h, w, _) in IMAGES)
+    assert (cov.cpu().numpy() == 1).all()
+    check_images(images, oracle_mod)
+    gb.close()
+
+
+def test_mixed_batches_replayed_from_one_graph_with_a_tuned_config(E, oracle_mod):
+    # a Mandelbrot batch and a Gaussian batch, each one persistent launch,
+    # captured together into one CUDA graph and replayed; the scheduler
+    # parameters come from the autotuner's result format
+    import torch
+    from paper_1805_02755_gb300.batching import GaussianBatch, MandelbrotBatch
+    views, images = make_views(torch), make_images(torch)
+    cfg = dict(scheduler="hguided", params=[1.0, 2.0], devices=16, ctas=0)
+    mb = MandelbrotBatch(views, config=cfg)
+    gb = GaussianBatch(images, config=cfg)
+    s = torch.cuda.Stream()
+    for b in (mb, gb):
+        b.engine.set_stream(s)
+    with torch.cuda.stream(s):
+        mb.run()
+        gb.run()
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        mb.run()
+        gb.run()
+    for v in views:
+        v["out"].fill_(-1)
+    for im in images:
+        im["out"].fill_(-1.0)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert mb.engine.plan_info()["devices"] == 16 and gb.engine.plan_info()["devices"] == 16
+    check_views(views, oracle_mod)
+    check_images(images, oracle_mod)
+    mb.close()
+    gb.close()
+
+
+def test_batch_tables_reject_bad_instances(E):
+    import torch
+    from paper_1805_02755_gb300.batching import GaussianBatch, MandelbrotBatch
+    ok = torch.zeros(64, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        MandelbrotBatch([dict(out=ok, W=8, H=9, x0=0, y0=0, dx=1, dy=1, max_iter=1)])  # 72 > 64 pixels
+    with pytest.raises(ValueError):
+        MandelbrotBatch([dict(out=ok[1:], W=4, H=4, x0=0, y0=0, dx=1, dy=1, max_iter=1)])  # misaligned
+    f = torch.zeros(64, device="cuda")
+    w = torch.zeros(30, device="cuda")
+    with pytest.raises(ValueError):
+        GaussianBatch([{"in": f, "out": f, "w": w, "W": 8, "H": 8}])  # 30 weights

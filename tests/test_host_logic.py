@@ -10,6 +10,38 @@ def test_instance_table_layout_matches_the_header():
     assert INSTANCE_DTYPE.fields["first"][1] == 56 and INSTANCE_DTYPE.fields["r"][1] == 72
 
 
+def test_view_and_image_tables_match_the_header():
+    # the offsets a C compiler gives ecl_mandelbrot_view and ecl_gaussian_image
+    # on a 64-bit target (checked against the header's own declarations)
+    import os
+    import subprocess
+    import tempfile
+    from paper_1805_02755_gb300.batching import IMAGE_DTYPE, VIEW_DTYPE
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = (
+        '#include <stddef.h>\n#include <stdio.h>\n#include "ecl.h"\nint main(void) {\n'
+        'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ecl_mandelbrot_view), '
+        'offsetof(ecl_mandelbrot_view, max_iter), offsetof(ecl_mandelbrot_view, first), '
+        'offsetof(ecl_mandelbrot_view, wgs), sizeof(ecl_gaussian_image), offsetof(ecl_gaussian_image, W), '
+        'offsetof(ecl_gaussian_image, first), offsetof(ecl_gaussian_image, tiles));\nreturn 0;\n}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "t.c"), os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(root, "include"), c, "-o", exe], check=True)
+        got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    v, i = VIEW_DTYPE.fields, IMAGE_DTYPE.fields
+    assert got == [VIEW_DTYPE.itemsize, v["max_iter"][1], v["first"][1], v["wgs"][1],
+                   IMAGE_DTYPE.itemsize, i["W"][1], i["first"][1], i["tiles"][1]]
+
+
+def test_batch_sizes_in_work_groups_and_tiles():
+    from paper_1805_02755_gb300.batching import GaussianBatch, MandelbrotBatch
+    assert MandelbrotBatch.workgroups(1024, 1024) == 1024 and MandelbrotBatch.workgroups(1, 1) == 1
+    assert MandelbrotBatch.workgroups(33, 31) == 1 and MandelbrotBatch.workgroups(1025, 1) == 2
+    assert GaussianBatch.tiles(224, 32) == 1 and GaussianBatch.tiles(225, 33) == 4 and GaussianBatch.tiles(1, 1) == 1
+    assert GaussianBatch.tiles(8192, 8192) == 256 * 37
+
+
 def test_split_uneven_sums_and_skews():
     from paper_1805_02755_gb300.batching import split_uneven
     for n, parts in [(1 << 20, 64), (1000, 7), (64, 64)]:
