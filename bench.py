@@ -18,11 +18,13 @@ Each program is one ecl_run() through the C ABI (one persistent launch).  The
 JSON line reports:
   value        work-items per second over the whole step (device-timed, inputs
                resident in HBM, L2 flushed before every step)
-  e2e          the same from pinned HOST memory through the package's API:
-               every step copies its inputs in and its results out inside the
-               timed region, the copies on two copy streams overlapped with
-               the computation (pipeline.Overlapped); e2e_sync: the same with
-               engines that copy in, compute and copy out before returning
+  e2e          the same from pinned HOST memory through the C ABI (host
+               buffers registered in the programs): every step copies its
+               inputs in and its results out inside the timed region, the
+               copies on two copy streams ordered around each launch by
+               events (ecl_engine_copy_streams), runs returning at once;
+               e2e_sync: the same with runs that copy in, compute and copy
+               out before returning
   roofline     the dominant kernel against its bound, with the ncu-measured
                DRAM traffic of a launch
   kernels      per program: time, work-items/s, own-unit rate, roofline
@@ -124,6 +126,8 @@ class Mandelbrot(Workload):
         self.npx = self.r["width"] * self.r["height"]
         self.lws = 256
         self.gws = self.npx // 4
+        self.config = dict(size="%dx%d" % (self.r["width"], self.r["height"]), max_iter=self.r["max_iter"],
+                           scheduler="static, 1 package")
 
     def setup(self):
         torch = self.torch
@@ -132,8 +136,6 @@ class Mandelbrot(Workload):
         self.d_out = [torch.zeros(self.npx, dtype=torch.int32, device="cuda")]
         self.h_in = []
         self.h_out = [torch.zeros(self.npx, dtype=torch.int32).pin_memory()]
-        self.config = dict(size="%dx%d" % (self.r["width"], self.r["height"]), max_iter=self.r["max_iter"],
-                           scheduler="static, 1 package")
 
     def program(self, ins, outs):
         r = self.r
@@ -199,6 +201,7 @@ class Gaussian(Workload):
         self.w = W.gaussian_weights(31, 5.0)
         self.lws = 128
         self.gws = self.H * self.Wd
+        self.config = dict(size="8192x8192", taps=31, sigma=5, scheduler="dynamic, 256 packages; devices autotuned")
 
     def setup(self):
         torch = self.torch
@@ -208,7 +211,6 @@ class Gaussian(Workload):
         self.d_out = [torch.zeros(self.H * self.Wd, dtype=torch.float32, device="cuda")]
         self.h_in = [torch.from_numpy(img).pin_memory(), torch.from_numpy(self.w).pin_memory()]
         self.h_out = [torch.zeros(self.H * self.Wd, dtype=torch.float32).pin_memory()]
-        self.config = dict(size="8192x8192", taps=31, sigma=5, scheduler="dynamic, 256 packages")
 
     def program(self, ins, outs):
         x, w = ins
@@ -292,6 +294,11 @@ class NBody(Workload):
         rng = W.rng(W.SEED_BASE + 20)
         self.fd_body = rng.choice(self.n, self.NFD, replace=False).astype(np.int32)
         self.fd_comp = rng.integers(0, 3, self.NFD).astype(np.int32)
+        self.config = dict(bodies=self.n, eps2=self.EPS2, lws=64,
+                           scheduler="hguided (force: k, minimum package and devices autotuned; energy, adjoint: "
+                                     "k=2 over 8 devices)",
+                           programs="nbody_acc + nbody_energy + nbody_adjoint (HGuided) + nbody_fd (256 samples, "
+                                    "h=1e-3, Static one package)")
 
     def setup(self):
         torch = self.torch
@@ -306,9 +313,6 @@ class NBody(Workload):
         self.h_in = [pos.pin_memory(), gE.pin_memory(), fb.pin_memory(), fc.pin_memory()]
         self.h_out = [torch.zeros((n, 4)).pin_memory(), torch.zeros(1, dtype=torch.float64).pin_memory(),
                       torch.zeros((n, 4)).pin_memory(), torch.zeros(self.NFD, dtype=torch.float64).pin_memory()]
-        self.config = dict(bodies=n, eps2=self.EPS2, lws=64, scheduler="hguided k=2 over 8 devices",
-                           programs="nbody_acc + nbody_energy + nbody_adjoint (HGuided) + nbody_fd (256 samples, "
-                                    "h=1e-3, Static one package)")
 
     def make_engine(self, sched, params, D=0, C=0, host=False):
         E = self.E
@@ -353,15 +357,23 @@ class NBody(Workload):
                     units=self.NFD)
 
     def cpu_sample(self, O, threads):
-        nb = 2048
+        nb, nfd = 2048, 16
+        n = self.n
         t = time.perf_counter()
         O.nbody_acc(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
         O.nbody_energy_grad(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
         O.nbody_potential(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
+        O.nbody_energy(self.pos, self.EPS2, threads=threads, rows=(0, nb))
+        O.nbody_fd_energy_grad(self.pos, self.EPS2, self.fd_body[:nfd], self.fd_comp[:nfd], 1e-3)
         secs = time.perf_counter() - t
-        # force and adjoint rows are each nb/n of their program; full potential rows stand in
-        # for the energy rows (twice the i<j work, so the sample overstates the energy's cost)
-        return nb / self.n, secs, "%d of %d bodies of the force, adjoint and potential rows" % (nb, self.n)
+        # work-items sampled: force and adjoint rows nb each; the energy's rows
+        # [0, nb) hold their share of the n(n-1)/2 pair terms of its n work-items;
+        # nfd of the finite-difference samples
+        pairs = nb * (n - 1) - nb * (nb - 1) // 2
+        wi = 2 * nb + n * pairs / (n * (n - 1) / 2) + nfd
+        return wi / self.work_items(), secs, (
+            "rows 0..%d of %d of the force, adjoint and energy (i<j) and %d of %d finite-difference samples"
+            % (nb - 1, n, nfd, self.NFD))
 
 
 class Binomial(Workload):
@@ -377,6 +389,9 @@ class Binomial(Workload):
         st = self.o["steps"].astype(np.int64)
         self.nodes = int((st * (st + 1) // 2).sum())
         self.nodes_price, self.nodes_adjoint = banded_node_updates(self.o)
+        self.config = dict(options=self.n, steps="U{256..2048}", scheduler="hguided k=2 over 8 devices",
+                           outputs="price + delta + vega", node_updates_full_lattice=self.nodes,
+                           node_updates_nonzero_band=self.nodes_price + self.nodes_adjoint)
 
     def setup(self):
         torch = self.torch
@@ -387,9 +402,6 @@ class Binomial(Workload):
         self.d_out = [torch.zeros(self.n, device="cuda"), torch.zeros((self.n, 2), device="cuda")]
         self.h_in = [t.pin_memory() for t in ts]
         self.h_out = [torch.zeros(self.n).pin_memory(), torch.zeros((self.n, 2)).pin_memory()]
-        self.config = dict(options=self.n, steps="U{256..2048}", scheduler="hguided k=2 over 8 devices",
-                           outputs="price + delta + vega", node_updates_full_lattice=self.nodes,
-                           node_updates_nonzero_band=self.nodes_price + self.nodes_adjoint)
 
     def program(self, ins, outs, greeks=True):
         S, K, T, sig, st = ins
@@ -510,6 +522,9 @@ class Gemm(Workload):
         self.gws = self.tiles * self.lws
         self.lws6 = 128 * 128
         self.gws6 = (self.M // 128) * (self.N // 128) * self.lws6
+        self.config = dict(M=self.M, N=self.N, K=self.K, tile="128x256x64", scheduler="hguided k=2 over 4 devices",
+                           programs="gemm_bf16 (bf16 inputs) + gemm_split3 (fp32 inputs, 3 products) + "
+                                    "gemm_split6 (fp32 inputs, 6 products, FP32 promotion every 64 of K, 128x128 tiles)")
 
     def setup(self):
         torch = self.torch
@@ -529,9 +544,6 @@ class Gemm(Workload):
         self.h_in = [ab.cpu().pin_memory(), bb.cpu().pin_memory(), A.pin_memory(), Bt.pin_memory()]
         self.h_out = [torch.zeros(self.M * self.N).pin_memory() for _ in range(2)]  # the step's programs
         del dA, dB
-        self.config = dict(M=self.M, N=self.N, K=self.K, tile="128x256x64", scheduler="hguided k=2 over 4 devices",
-                           programs="gemm_bf16 (bf16 inputs) + gemm_split3 (fp32 inputs, 3 products) + "
-                                    "gemm_split6 (fp32 inputs, 6 products, FP32 promotion every 64 of K, 128x128 tiles)")
 
     def make_engine(self, sched, params, D=0, C=0, host=False):
         E = self.E
@@ -625,6 +637,8 @@ class Ray(Workload):
         self.Wd = self.Hd = 1024 if SMALL else 2048
         self.lws = 128
         self.gws = self.Wd * self.Hd
+        self.config = dict(size="%dx%d" % (self.Wd, self.Hd), spheres=self.sc["nspheres"], lights=self.sc["nlights"],
+                           max_depth=self.sc["max_depth"], scheduler="hguided k=2, one device")
 
     def setup(self):
         torch = self.torch
@@ -634,8 +648,6 @@ class Ray(Workload):
         self.d_out = [torch.zeros((self.gws, 4), device="cuda")]
         self.h_in = [s.pin_memory()]
         self.h_out = [torch.zeros((self.gws, 4)).pin_memory()]
-        self.config = dict(size="%dx%d" % (self.Wd, self.Hd), spheres=self.sc["nspheres"], lights=self.sc["nlights"],
-                           max_depth=self.sc["max_depth"], scheduler="hguided k=2, one device")
 
     def program(self, ins, outs):
         sc = self.sc
@@ -938,12 +950,14 @@ def run_ours(args):
         kern["gemm_split6"]["compensated_over_plain"] = kern["gemm_split6"]["ms"] / kern["gemm_bf16"]["ms"]
 
     # End to end from pinned host memory, every step: the inputs copied in, the
-    # programs run, the results copied out.  Measured two ways through the
-    # package's API: (1) pipeline.Overlapped, the copies on two copy streams
-    # overlapped with the other configurations' computation (the "e2e" value);
-    # (2) engines with host buffers, each run copying in, computing and copying
-    # out before it returns (the synchronous run of Listing 1, "e2e_sync").
-    from paper_1805_02755_gb300 import pipeline as PL
+    # programs run, the results copied out, all through the C ABI with host
+    # buffers registered in the programs.  Measured two ways: (1) "e2e": every
+    # engine's copies on two copy streams (ecl_engine_copy_streams), ordered
+    # around its launch by events, each run returning at once; the copies of
+    # one configuration overlap another's computation and the step ends when
+    # every result is in host memory; (2) "e2e_sync": each run copies in,
+    # computes and copies out before it returns (the synchronous run of
+    # Listing 1).
     swls = [w for w in wls if w.in_step]
     h2d = sum(t.numel() * t.element_size() for w in swls for t in w.h_in)
     d2h = sum(t.numel() * t.element_size() for w in swls for t in w.h_out)
@@ -956,18 +970,11 @@ def run_ours(args):
     def out_bytes(w):
         return sum(t.numel() * t.element_size() for t in w.h_out)
 
+    def engines_of(x):
+        return x.engs if isinstance(x, MultiEngine) else [x]
+
     first = max(swls, key=dev_ms)
     order = [first] + sorted((w for w in swls if w is not first), key=out_bytes, reverse=True)
-    ov = PL.Overlapped([PL.Stage(w.eng, zip(w.d_in, w.h_in), zip(w.h_out, w.d_out)) for w in order])
-    assert ov.bytes_in == h2d and ov.bytes_out == d2h
-    for _ in range(max(1, args.warmup)):
-        ov.run()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ov.run()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
-
     for _ in range(max(1, args.warmup)):
         for w in swls:
             w.host.run()
@@ -1000,6 +1007,26 @@ def run_ours(args):
             per_cfg_dev[w.name] += ea.elapsed_time(eb) * 1e-3
     e2e_sync_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
 
+    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
+    for w in order:
+        for e in engines_of(w.host):
+            e.copy_streams(copy_in, copy_out, asynchronous=True)
+
+    def e2e_step():
+        for w in order:
+            w.host.run()  # enqueues copies in, the launch and copies out; returns at once
+        for w in order:
+            for e in engines_of(w.host):
+                e.synchronize()  # this step's results are in host memory
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+
     total_wi = sum(wi for _, _, _, wi in progs)
     value = job_rate(total_wi, world, step_ms * 1e-3)
     rf = dict(kern[dominant]["roofline"])
@@ -1021,16 +1048,15 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": step_ms, "ms_per_step_quantiles": quantiles(tot),
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, shaped like the paper's workloads)",
-        "config": {"workload": "+".join(w.name for w in swls), "programs": {w.name: w.config for w in swls},
-                   "beside_the_step": {w.name: w.config for w in wls if not w.in_step},
-                   "l2": "flushed (512 MiB write) before every step", "parallelism": "replicas"},
+        "config": step_config(wls),
         "e2e": {"value": job_rate(total_wi, world, e2e_s), "unit": "work-items/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
-                "how": "pipeline.Overlapped: copies on two copy streams overlapped with computation",
-                "stage_order": [w.name for w in order]},
+                "how": "C ABI, host buffers: ecl_engine_copy_streams (copies on two copy streams, "
+                       "event-ordered around each launch, asynchronous runs); one synchronize per engine ends "
+                       "each step", "stage_order": [w.name for w in order]},
         "e2e_sync": {"value": job_rate(total_wi, world, e2e_sync_s), "unit": "work-items/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_sync_s * 1e3,
-                     "how": "engines with host buffers: each run copies in, computes, copies out, then returns",
+                     "how": "C ABI, host buffers: each run copies in, computes, copies out, then returns",
                      "ms_per_config": {k: v * 1e3 / args.steps for k, v in per_cfg.items()},
                      "device_ms_per_config": {k: v * 1e3 / args.steps for k, v in per_cfg_dev.items()},
                      "h2d_gbs_largest_input": link_gbs},
@@ -1061,8 +1087,6 @@ def apply_tuned(w, name, config):
         else:
             AT.apply(eng, config)
     w.tuned_config = config
-    w.config = dict(w.config, scheduler="autotuned: %s %s, %d devices x %s CTAs" % (
-        config["scheduler"], config["params"], config["devices"], config["ctas"] or "all"))
 
 
 def autotune_report(w, name):
@@ -1073,7 +1097,11 @@ def autotune_report(w, name):
     make, gws, lws = w.tunable(name)
     s, p, D, C = w.sched
     default = dict(scheduler=s, params=list(p), devices=D, ctas=C)
-    space = AT.default_space(name, gws // lws)
+    # the configuration fixes the scheduler (and Dynamic's package count):
+    # the search varies what it leaves free (devices, CTAs per device, and
+    # HGuided's k and minimum package)
+    space = [c for c in AT.default_space(name, gws // lws) if c["scheduler"] == s and
+             (s != "dynamic" or list(c["params"]) == list(p))]
     if default not in space:
         space.append(default)
     res = AT.autotune(name, make, gws, lws, space=space, reps=3, warmup=1)
@@ -1126,6 +1154,14 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
+def step_config(wls):
+    """The workload's description, the same for both arms."""
+    swls = [w for w in wls if w.in_step]
+    return {"workload": "+".join(w.name for w in swls), "programs": {w.name: w.config for w in swls},
+            "beside_the_step": {w.name: w.config for w in wls if not w.in_step},
+            "l2": "flushed (512 MiB write) before every step", "parallelism": "replicas"}
+
+
 def cpu_baseline(wls, total_wi, args):
     """Oracle on the host cores: a bounded sample of each program, scaled to the full step."""
     import oracle
@@ -1138,7 +1174,7 @@ def cpu_baseline(wls, total_wi, args):
         full_s += secs / frac
         samples.append("%s: %s in %.2fs" % (w.name, what, secs))
     return dict(value=total_wi / full_s, unit="work-items/s", cores=threads, kind="oracle",
-                sample="; ".join(samples))
+                sample="; ".join(samples) + " (the full step's time projected from these samples)")
 
 
 def run_reference(args):
@@ -1151,33 +1187,45 @@ def run_reference(args):
     threads = oracle.default_threads()
 
     names = args.only.split(",") if args.only else None
-    wls = []
+    allw = []
     for cls in WORKLOADS:
-        if (names is None and cls.in_step) or (names is not None and cls.name in names):
+        if names is None or cls.name in names:
             w = cls(None, None, 0)
             w.host_setup()
-            wls.append(w)
+            allw.append(w)
+    if names is not None and not any(w.in_step for w in allw):
+        for w in allw:
+            w.in_step = True
+    wls = [w for w in allw if w.in_step]  # sampled; the rest only describe the configuration
     total_wi = sum(w.work_items() for w in wls)
-    times = []
-    what = {}
+    # a step is one bounded sample of every program of the workload: its time
+    # is the measured time of that sample, its work the sampled work-items
+    times, wis = [], []
+    what, frac = {}, {}
     for i in range(args.warmup + args.steps):
-        full = 0.0
+        secs_step, wi_step = 0.0, 0.0
         for w in wls:
-            frac, secs, desc = w.cpu_sample(oracle, threads)
-            what[w.name] = desc
-            full += secs / frac
+            f, secs, desc = w.cpu_sample(oracle, threads)
+            what[w.name], frac[w.name] = desc, f
+            secs_step += secs
+            wi_step += f * w.work_items()
         if i >= args.warmup:
-            times.append(full)
+            times.append(secs_step)
+            wis.append(wi_step)
     step_s = statistics.median(times)
-    val = total_wi / step_s
+    val = statistics.median(wi / t for wi, t in zip(wis, times))
     samples = "; ".join("%s: %s" % kv for kv in what.items())
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "work-items/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "+".join(w.name for w in wls)},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, shaped like the "
+        "paper's workloads)",
+        "config": step_config(allw),
+        "step": "one bounded sample of every program per step (ms_per_step is its measured time); the full "
+                "step of %d work-items would take %.0f s at this rate" % (total_wi, total_wi / val),
+        "sampled_fraction": frac,
         "cpu_baseline": {"value": val, "unit": "work-items/s", "cores": threads, "kind": "oracle",
-                         "sample": samples + " (each step: bounded samples scaled to the full step)"},
+                         "sample": samples},
         "e2e": {"value": val, "unit": "work-items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

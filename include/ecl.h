@@ -161,6 +161,21 @@ void ecl_engine_destroy(ecl_engine *e);
 /* Replaces the stream used by later calls. */
 ecl_status ecl_engine_set_stream(ecl_engine *e, void *cuda_stream);
 
+/* Copy streams for host buffers (the asynchronous enqueueing and event
+ * chaining of Sec. 5.1, for the copies of the Buffer proxy of Sec. 4.2).
+ * With them set, a run of a program with host buffers issues the copies in
+ * on `h2d_stream` and the copies out on `d2h_stream` (NULL = the engine's
+ * stream), ordered around the launch by events: the launch waits for the
+ * copies in, the copies out wait for the launch, and the next run's copies
+ * in wait for this run's launch (its kernel reads the device mirrors) and
+ * its launch for this run's copies out.  async != 0: ecl_run returns once
+ * everything is enqueued, without waiting; ecl_synchronize (or ecl_stats)
+ * waits for the copies out and reports device errors.  So runs of several
+ * engines, each with its own host buffers, overlap one engine's copies with
+ * another's computation when the host memory is page-locked.  async == 0
+ * keeps the synchronous run of Listing 1.  Errors: ECL_ERR_ARG, ECL_ERR_CUDA. */
+ecl_status ecl_engine_copy_streams(ecl_engine *e, void *h2d_stream, void *d2h_stream, int async);
+
 /* Global and local work size (Listing 2 "work_items"; Listing 1 sets them
  * one at a time).  gws must be a positive multiple of lws; each kernel
  * also restricts lws (see the kernel list below).  G = gws / lws. */

@@ -165,12 +165,15 @@ def nbody_step(pos4, vel4, dt: float, eps2: float, threads: Optional[int] = None
     return po, vo
 
 
-def nbody_energy(pos4: np.ndarray, eps2: float, threads: Optional[int] = None) -> float:
-    """E = -sum_{i<j} m_i m_j (r_ij^2 + eps2)^(-1/2), partial sums added in FP64."""
+def nbody_energy(pos4: np.ndarray, eps2: float, threads: Optional[int] = None, rows=None) -> float:
+    """E = -sum_{i<j} m_i m_j (r_ij^2 + eps2)^(-1/2), partial sums added in FP64.
+
+    rows=(b, e) sums only the terms of rows i in [b, e) (all j > i)."""
     L = lib()
     pos4 = _c(pos4, np.float32)
     n = pos4.shape[0]
-    parts = _run(lambda i0, i1: L.ecl_oracle_nbody_energy(_ptr(pos4), n, eps2, i0, i1), 0, n, threads)
+    b, e = rows if rows is not None else (0, n)
+    parts = _run(lambda i0, i1: L.ecl_oracle_nbody_energy(_ptr(pos4), n, eps2, i0, i1), b, e, threads)
     return float(sum(parts))
 
 

@@ -62,6 +62,7 @@ def lib():
             "ecl_engine_create": (_st, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
             "ecl_engine_destroy": (None, [_vp]),
             "ecl_engine_set_stream": (_st, [_vp, _vp]),
+            "ecl_engine_copy_streams": (_st, [_vp, _vp, _vp, ctypes.c_int]),
             "ecl_work_items": (_st, [_vp, ctypes.c_uint64, ctypes.c_uint32]),
             "ecl_scheduler": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
             "ecl_workers": (_st, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -140,6 +141,12 @@ def ecl_engine_destroy(e) -> None:
 
 def ecl_engine_set_stream(e, cuda_stream) -> None:
     _check(lib().ecl_engine_set_stream(e, _vp(_stream_handle(cuda_stream))), e)
+
+
+def ecl_engine_copy_streams(e, h2d_stream=None, d2h_stream=None, asynchronous: bool = True) -> None:
+    h2d = 0 if h2d_stream is None else _stream_handle(h2d_stream)  # None: the engine's own stream
+    d2h = 0 if d2h_stream is None else _stream_handle(d2h_stream)
+    _check(lib().ecl_engine_copy_streams(e, _vp(h2d), _vp(d2h), 1 if asynchronous else 0), e)
 
 
 def ecl_work_items(e, gws: int, lws: int) -> None:
@@ -479,6 +486,13 @@ class Engine:
 
     def set_stream(self, stream):
         ecl_engine_set_stream(self.h, stream)
+        return self
+
+    def copy_streams(self, h2d=None, d2h=None, asynchronous: bool = True):
+        """Host-buffer copies on their own streams, event-ordered around the
+        launch; with asynchronous=True run() returns at once and
+        synchronize() waits for the results (include/ecl.h)."""
+        ecl_engine_copy_streams(self.h, h2d, d2h, asynchronous)
         return self
 
     def run(self):

@@ -24,7 +24,7 @@ def default_space(kernel: str, G: int, device: int = 0) -> List[Dict]:
     sms, per_sm = ecl_kernel_occupancy(kernel, device)
     resident = sms * max(1, per_sm)
     space = []
-    for D in sorted({1, 4, 8, 16, 64, resident}):
+    for D in sorted({1, 4, 8, 12, 16, 24, 64, resident}):
         if D > resident:
             continue
         C = 0  # automatic: fill the GPU
@@ -33,7 +33,7 @@ def default_space(kernel: str, G: int, device: int = 0) -> List[Dict]:
                 if mn > max(1, G // max(1, D)):
                     continue
                 space.append(dict(scheduler="hguided", params=[k, mn], devices=D, ctas=C))
-        for npk in (64, 256, 1024):
+        for npk in (64, 256, 1024):  # 256: the Gaussian configuration's package count
             if npk <= G:
                 space.append(dict(scheduler="dynamic", params=[npk], devices=D, ctas=C))
     return space

@@ -143,6 +143,12 @@ struct ecl_engine {
     uint32_t spin_limit = 20000000u;  // ecl_debug knobs
     uint32_t withhold = 0;
     Workspace ws;
+    // host buffers: optional copy streams, and whether a run returns before
+    // its copies finish (ecl_engine_copy_streams)
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    bool copies_set = false, host_async = false;
+    cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_out = nullptr;
+    bool ev_pending = false;  // ev_done / ev_out record a run not yet waited for
     // facts of the last run
     uint64_t last_G = 0, last_npkg = 0;
     uint32_t last_D = 0, last_C = 0, last_grid = 0, last_mode = MODE_MONO;
@@ -344,6 +350,10 @@ ecl_status check_device_error(ecl_engine *e)
 {
     CUDA_OR_FAIL(e, cudaMemcpyAsync(e->q_host, e->q, sizeof(Queue), cudaMemcpyDeviceToHost, e->stream));
     CUDA_OR_FAIL(e, cudaStreamSynchronize(e->stream));
+    if (e->ev_pending) {  // the output copies of the last run, on the copy stream
+        CUDA_OR_FAIL(e, cudaEventSynchronize(e->ev_out));
+        e->ev_pending = false;
+    }
     if (e->q_host->error) {
         const unsigned long long info = e->q_host->error_info;
         // the run is void: put the queue back in its initial state
@@ -407,7 +417,27 @@ void ecl_engine_destroy(ecl_engine *e)
     cudaFree(e->ws.ptr);
     cudaFreeHost(e->q_host);
     cudaFreeHost(e->stage);
+    if (e->ev_out) cudaEventSynchronize(e->ev_out);
+    for (cudaEvent_t ev : {e->ev_in, e->ev_done, e->ev_out})
+        if (ev) cudaEventDestroy(ev);
     delete e;
+}
+
+ecl_status ecl_engine_copy_streams(ecl_engine *e, void *h2d_stream, void *d2h_stream, int async)
+{
+    if (!e) return ECL_ERR_ARG;
+    CUDA_OR_FAIL(e, cudaSetDevice(e->device));
+    if (e->ev_pending) {
+        CUDA_OR_FAIL(e, cudaEventSynchronize(e->ev_out));
+        e->ev_pending = false;
+    }
+    for (cudaEvent_t *ev : {&e->ev_in, &e->ev_done, &e->ev_out})
+        if (!*ev) CUDA_OR_FAIL(e, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    e->h2d = (cudaStream_t)h2d_stream;
+    e->d2h = (cudaStream_t)d2h_stream;
+    e->copies_set = true;
+    e->host_async = async != 0;
+    return ECL_OK;
 }
 
 ecl_status ecl_engine_set_stream(ecl_engine *e, void *cuda_stream)
@@ -825,8 +855,24 @@ ecl_status ecl_run(ecl_engine *e)
     }
     s.q = e->q;
 
-    for (Buf *b : host_in)
-        CUDA_OR_FAIL(e, cudaMemcpyAsync(b->mirror, b->ptr, b->bytes, cudaMemcpyHostToDevice, e->stream));
+    const bool copies = e->copies_set && (!host_in.empty() || !host_out.empty());
+    cudaStream_t h2d = e->h2d ? e->h2d : e->stream, d2h = e->d2h ? e->d2h : e->stream;
+    if (copies && e->ev_pending) {
+        // the previous run's kernel reads the input mirrors and its output
+        // copies read the output mirrors: new copies in wait for the kernel,
+        // the new kernel waits for the copies out
+        CUDA_OR_FAIL(e, cudaStreamWaitEvent(h2d, e->ev_done, 0));
+        CUDA_OR_FAIL(e, cudaStreamWaitEvent(e->stream, e->ev_out, 0));
+    }
+    if (copies && !host_in.empty()) {
+        for (Buf *b : host_in)
+            CUDA_OR_FAIL(e, cudaMemcpyAsync(b->mirror, b->ptr, b->bytes, cudaMemcpyHostToDevice, h2d));
+        CUDA_OR_FAIL(e, cudaEventRecord(e->ev_in, h2d));
+        CUDA_OR_FAIL(e, cudaStreamWaitEvent(e->stream, e->ev_in, 0));
+    } else {
+        for (Buf *b : host_in)
+            CUDA_OR_FAIL(e, cudaMemcpyAsync(b->mirror, b->ptr, b->bytes, cudaMemcpyHostToDevice, e->stream));
+    }
     LaunchCtx lc;
     lc.stream = e->stream;
     lc.lws = e->lws;
@@ -842,6 +888,15 @@ ecl_status ecl_run(ecl_engine *e)
     e->last_grid = grid;
     e->last_mode = pl.mode;
     e->ran = true;
+    if (copies) {
+        CUDA_OR_FAIL(e, cudaEventRecord(e->ev_done, e->stream));
+        CUDA_OR_FAIL(e, cudaStreamWaitEvent(d2h, e->ev_done, 0));
+        for (Buf *b : host_out)
+            CUDA_OR_FAIL(e, cudaMemcpyAsync(b->ptr, b->mirror, b->bytes, cudaMemcpyDeviceToHost, d2h));
+        CUDA_OR_FAIL(e, cudaEventRecord(e->ev_out, d2h));
+        e->ev_pending = true;
+        return e->host_async ? ECL_OK : check_device_error(e);
+    }
     if (!host_out.empty() || !host_in.empty()) {
         for (Buf *b : host_out)
             CUDA_OR_FAIL(e, cudaMemcpyAsync(b->ptr, b->mirror, b->bytes, cudaMemcpyDeviceToHost, e->stream));

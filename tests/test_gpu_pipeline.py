@@ -56,3 +56,48 @@ def test_overlapped_stages_match_the_oracle(E, oracle_mod):
         assert np.all(np.abs(g - g_ref) <= 1e-5 * np.abs(g_ref))
     e1.close()
     e2.close()
+
+
+def test_c_abi_copy_streams_asynchronous_runs(E, oracle_mod):
+    # Two engines with host (pinned) buffers, copies on two copy streams,
+    # asynchronous runs: the Gaussian input changes between runs, so a copy
+    # in that overtook the previous run's kernel, or a kernel that overtook
+    # the previous run's copy out, would show in the results.
+    import torch
+    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
+    Wd, H = 320, 192
+    w = torch.from_numpy(W.gaussian_weights()).pin_memory()
+    imgs = [W.gaussian_image(H, Wd, seed=1200 + i) for i in range(4)]
+    g_in = torch.zeros(H * Wd).pin_memory()
+    g_out = torch.zeros(H * Wd).pin_memory()
+    eg = E.Engine(0)
+    eg.work_items(H * Wd, 128).scheduler("dynamic", (16,)).workers(8, 0)
+    eg.program(E.Program("gaussian").in_(g_in).in_(w).out(g_out).args(g_in, w, g_out, Wd, H, 31))
+    eg.copy_streams(copy_in, copy_out, asynchronous=True)
+    mw, mh, it = 512, 128, 300
+    m_out = torch.zeros(mw * mh, dtype=torch.int32).pin_memory()
+    em = E.Engine(0)
+    em.work_items(mw * mh // 4, 256).scheduler("hguided", (2.0, 1.0)).workers(8, 0)
+    em.program(E.Program("mandelbrot").out(m_out).args(m_out, mw, mh, -2.0, -1.0, 3.0 / mw, 2.0 / mh, it))
+    em.copy_streams(copy_in, copy_out, asynchronous=True)
+    mref = oracle_mod.mandelbrot(mw, mh, -2.0, -1.0, np.float32(3.0 / mw), np.float32(2.0 / mh), it)
+    for img in imgs:
+        g_in.copy_(torch.from_numpy(img))
+        eg.run()
+        em.run()
+        eg.synchronize()
+        em.synchronize()
+        ref = oracle_mod.gaussian(img, W.gaussian_weights())
+        got = g_out.numpy().reshape(H, Wd)
+        assert (np.abs(got - ref) <= 1e-5 * np.abs(ref)).all()
+        assert np.array_equal(m_out.numpy().view(np.uint32).reshape(mh, mw), mref)
+        g_out.zero_()
+        m_out.zero_()
+    # back to synchronous runs with the copies on the copy streams
+    eg.copy_streams(copy_in, copy_out, asynchronous=False)
+    g_in.copy_(torch.from_numpy(imgs[0]))
+    eg.run()
+    ref = oracle_mod.gaussian(imgs[0], W.gaussian_weights())
+    assert (np.abs(g_out.numpy().reshape(H, Wd) - ref) <= 1e-5 * np.abs(ref)).all()
+    eg.close()
+    em.close()

@@ -79,5 +79,12 @@ def test_reference_arm_prints_on_rank_zero_only(rank, prints):
         assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
         assert d["cpu_baseline"]["value"] == d["value"]
         assert d["e2e"] == dict(value=d["value"], unit=d["unit"], h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+        # the same configuration description as the kernel arm's line, and the
+        # sample each step times
+        import bench
+        w = bench.Mandelbrot(None, None, 0)
+        w.host_setup()
+        assert d["config"] == json.loads(json.dumps(bench.step_config([w])))
+        assert d["sampled_fraction"] == {"mandelbrot": 1.0}
     else:
         assert lines == []
