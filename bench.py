@@ -60,6 +60,9 @@ EXTRA_PROGRAMS = {"gemm_split6"}
 NCU_TRAFFIC = {}
 METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
 L2_FLUSH_BYTES = 512 << 20
+# the oracle's bounded sample: the same fraction of every program's work-items,
+# so that the sample has the step's mix (a few seconds of oracle work on 16 cores)
+CPU_SAMPLE = 1.0 / 1024
 SMS_NOMINAL = 152
 SM_MAX_MHZ = 2070.0
 
@@ -183,12 +186,17 @@ class Mandelbrot(Workload):
                     ms_batched_graph_replay=ms_graph, batched_over_plain=ms_batched / ms_plain,
                     scheduler="batched: hguided k=2, min 1, every resident CTA a device")
 
-    def cpu_sample(self, O, threads):
+    def cpu_sample(self, O, threads, f):
+        # k evenly spaced rows, each through the oracle as a one-row image
         r = self.r
+        k = max(1, int(round(r["height"] * f)))
+        rows = [int((i + 0.5) * r["height"] / k) for i in range(k)]
         t = time.perf_counter()
-        O.mandelbrot(r["width"], r["height"], np.float32(r["x0"]), np.float32(r["y0"]), np.float32(r["dx"]),
-                     np.float32(r["dy"]), r["max_iter"], threads=threads)
-        return 1.0, time.perf_counter() - t, "all 1024 rows"
+        for j in rows:
+            cy = np.float32(np.float32(r["y0"]) + np.float32(j) * np.float32(r["dy"]))
+            O.mandelbrot(r["width"], 1, np.float32(r["x0"]), cy, np.float32(r["dx"]), np.float32(r["dy"]),
+                         r["max_iter"], threads=threads)
+        return k / r["height"], time.perf_counter() - t, "%d evenly spaced of %d rows" % (k, r["height"])
 
 
 class Gaussian(Workload):
@@ -264,10 +272,11 @@ class Gaussian(Workload):
                     ms_batched_graph_replay=ms_graph, batched_over_plain=ms_batched / ms_plain,
                     config=cfg or dict(scheduler=s, params=list(p), devices=D, ctas=C))
 
-    def cpu_sample(self, O, threads):
+    def cpu_sample(self, O, threads, f):
+        k = max(1, int(round(self.H * f)))
         t = time.perf_counter()
-        O.gaussian(self.img, self.w, rows=(0, 2048), threads=threads)
-        return 2048 / self.H, time.perf_counter() - t, "2048 of %d rows" % self.H
+        O.gaussian(self.img, self.w, rows=(0, k), threads=threads)
+        return k / self.H, time.perf_counter() - t, "%d of %d rows" % (k, self.H)
 
 
 def _single_program_tunable(self, name):
@@ -356,24 +365,25 @@ class NBody(Workload):
         return dict(bound="alu", inst=16.0 * n * self.NFD, flops=18.0 * n * self.NFD, unit_name="samples/s",
                     units=self.NFD)
 
-    def cpu_sample(self, O, threads):
-        nb, nfd = 2048, 16
+    def cpu_sample(self, O, threads, f):
         n = self.n
+        nb, nfd = max(1, int(round(n * f))), max(1, int(round(self.NFD * f)))
+        m = max(1, int(round(n * f / 2)))  # energy rows 0..m-1: about f of the i<j pairs
         t = time.perf_counter()
         O.nbody_acc(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
         O.nbody_energy_grad(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
         O.nbody_potential(self.pos, self.EPS2, bodies=(0, nb), threads=threads)
-        O.nbody_energy(self.pos, self.EPS2, threads=threads, rows=(0, nb))
+        O.nbody_energy(self.pos, self.EPS2, threads=threads, rows=(0, m))
         O.nbody_fd_energy_grad(self.pos, self.EPS2, self.fd_body[:nfd], self.fd_comp[:nfd], 1e-3)
         secs = time.perf_counter() - t
         # work-items sampled: force and adjoint rows nb each; the energy's rows
         # [0, nb) hold their share of the n(n-1)/2 pair terms of its n work-items;
         # nfd of the finite-difference samples
-        pairs = nb * (n - 1) - nb * (nb - 1) // 2
+        pairs = m * (n - 1) - m * (m - 1) // 2
         wi = 2 * nb + n * pairs / (n * (n - 1) / 2) + nfd
         return wi / self.work_items(), secs, (
-            "rows 0..%d of %d of the force, adjoint and energy (i<j) and %d of %d finite-difference samples"
-            % (nb - 1, n, nfd, self.NFD))
+            "rows 0..%d of %d of the force and adjoint, rows 0..%d of the energy (i<j), %d of %d "
+            "finite-difference samples" % (nb - 1, n, m - 1, nfd, self.NFD))
 
 
 class Binomial(Workload):
@@ -474,9 +484,9 @@ class Binomial(Workload):
                     units=self.n, extra={"node_updates_per_s": nb,
                                          "full_lattice_node_updates_per_s": 2 * self.nodes})
 
-    def cpu_sample(self, O, threads):
+    def cpu_sample(self, O, threads, f):
         t = time.perf_counter()
-        k = 512 * threads
+        k = max(1, int(round(self.n * f)))
         o = self.o
         O.binomial(o["S"][:k], o["K"][:k], o["T"][:k], o["sigma"][:k], o["steps"][:k], o["r"], threads=threads)
         return k / self.n, time.perf_counter() - t, "%d of %d options (price, delta, vega)" % (k, self.n)
@@ -573,9 +583,9 @@ class Gemm(Workload):
         nprod = 6.0 if name == "gemm_split6" else 3.0
         return dict(bound="tensor", flops=nprod * f, unit_name="effective TFLOP/s", units=f / 1e12)
 
-    def cpu_sample(self, O, threads):
+    def cpu_sample(self, O, threads, f):
         rng = W.rng(5)
-        ne = 4096
+        ne = max(1, int(round(self.M * self.N * f)))
         ii = rng.integers(0, self.M, ne)
         jj = rng.integers(0, self.N, ne)
         t = time.perf_counter()
@@ -662,9 +672,9 @@ class Ray(Workload):
         return dict(bound="alu", inst=16.0 * tests, flops=16.0 * tests, unit_name="pixels/s", units=self.gws,
                     extra={"rays_per_s": rays, "ray_sphere_tests_per_s": tests})
 
-    def cpu_sample(self, O, threads):
+    def cpu_sample(self, O, threads, f):
         sc = self.sc
-        rows = 32
+        rows = max(2, 2 * int(round(self.Hd * f / 2)))
         t = time.perf_counter()
         O.ray(sc["scene"], sc["nspheres"], sc["nlights"], self.Wd, self.Hd, sc["ka"], sc["bg"], sc["max_depth"],
               rows=(self.Hd // 2 - rows // 2, self.Hd // 2 + rows // 2), threads=threads)
@@ -687,19 +697,7 @@ class MandelbrotLarge(Mandelbrot):
         self.npx = self.r["width"] * self.r["height"]
         self.lws = 256
         self.gws = self.npx // 4
-
-    def cpu_sample(self, O, threads):
-        # 64 evenly spaced rows, each through the oracle as a one-row image at
-        # that row's c_y (float32, as the kernel forms it)
-        r = self.r
-        rows = list(range(0, r["height"], r["height"] // 64))
-        t = time.perf_counter()
-        for j in rows:
-            cy = np.float32(r["y0"]) + np.float32(j) * np.float32(r["dy"])
-            O.mandelbrot(r["width"], 1, np.float32(r["x0"]), cy, np.float32(r["dx"]), np.float32(r["dy"]),
-                         r["max_iter"], threads=threads)
-        return len(rows) / r["height"], time.perf_counter() - t, "%d evenly spaced of %d rows" % (
-            len(rows), r["height"])
+        self.config = dict(size="%dx%d" % (n, n), max_iter=1024, scheduler="static, 1 package")
 
 
 WORKLOADS = [Mandelbrot, Gaussian, NBody, Binomial, Gemm, Ray, MandelbrotLarge]
@@ -1170,7 +1168,7 @@ def cpu_baseline(wls, total_wi, args):
     full_s = 0.0
     samples = []
     for w in wls:
-        frac, secs, what = w.cpu_sample(oracle, threads)
+        frac, secs, what = w.cpu_sample(oracle, threads, CPU_SAMPLE)
         full_s += secs / frac
         samples.append("%s: %s in %.2fs" % (w.name, what, secs))
     return dict(value=total_wi / full_s, unit="work-items/s", cores=threads, kind="oracle",
@@ -1205,7 +1203,7 @@ def run_reference(args):
     for i in range(args.warmup + args.steps):
         secs_step, wi_step = 0.0, 0.0
         for w in wls:
-            f, secs, desc = w.cpu_sample(oracle, threads)
+            f, secs, desc = w.cpu_sample(oracle, threads, CPU_SAMPLE)
             what[w.name], frac[w.name] = desc, f
             secs_step += secs
             wi_step += f * w.work_items()

@@ -82,7 +82,7 @@ def test_c_abi_copy_streams_asynchronous_runs(E, oracle_mod):
     em.copy_streams(copy_in, copy_out, asynchronous=True)
     mref = oracle_mod.mandelbrot(mw, mh, -2.0, -1.0, np.float32(3.0 / mw), np.float32(2.0 / mh), it)
     for img in imgs:
-        g_in.copy_(torch.from_numpy(img))
+        g_in.copy_(torch.from_numpy(img.reshape(-1)))
         eg.run()
         em.run()
         eg.synchronize()
@@ -95,7 +95,7 @@ def test_c_abi_copy_streams_asynchronous_runs(E, oracle_mod):
         m_out.zero_()
     # back to synchronous runs with the copies on the copy streams
     eg.copy_streams(copy_in, copy_out, asynchronous=False)
-    g_in.copy_(torch.from_numpy(imgs[0]))
+    g_in.copy_(torch.from_numpy(imgs[0].reshape(-1)))
     eg.run()
     ref = oracle_mod.gaussian(imgs[0], W.gaussian_weights())
     assert (np.abs(g_out.numpy().reshape(H, Wd) - ref) <= 1e-5 * np.abs(ref)).all()

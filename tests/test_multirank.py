@@ -85,6 +85,6 @@ def test_reference_arm_prints_on_rank_zero_only(rank, prints):
         w = bench.Mandelbrot(None, None, 0)
         w.host_setup()
         assert d["config"] == json.loads(json.dumps(bench.step_config([w])))
-        assert d["sampled_fraction"] == {"mandelbrot": 1.0}
+        assert d["sampled_fraction"] == {"mandelbrot": bench.CPU_SAMPLE}  # one row of 1024
     else:
         assert lines == []
