@@ -57,7 +57,10 @@ SMALL = False  # --small: reduced sizes for profiler captures (never a bench val
 EXTRA_PROGRAMS = {"gemm_split6"}
 
 # ncu-measured DRAM bytes per launch of the dominant kernel (null once the kernel changes)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "binomial": {"bytes_per_launch": 705.536e3 * 64,
+                 "source": "profiles/binomial_greeks_16384_options.md (16384 options x 64)"},
+}
 METRIC = ("work-items/s & % of roofline per kernel; sched overhead vs 1 launch; Δ vs plain")
 L2_FLUSH_BYTES = 512 << 20
 # the oracle's bounded sample: the same fraction of every program's work-items,
