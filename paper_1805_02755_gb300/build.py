@@ -37,6 +37,29 @@ SOURCES = {
     "k_probe.cu": [],
 }
 HEADERS = ["ecl_internal.h", "sched.cuh", "f32x2.cuh", "tc.cuh"]
+LFACT = "lfact_table.inc"  # generated into _build: ln k! for k = 0..2048 as FP32 (hi, lo) pairs
+
+
+def write_lfact_table(path: str, kmax: int = 2048) -> None:
+    """ln k! (math.lgamma(k + 1), double precision) split into two FP32
+    values hi + lo, written as C hex-float initialisers for the binomial
+    kernel's closed-form leaf weights."""
+    import math
+    import struct
+
+    def f32(x: float) -> float:
+        return struct.unpack("<f", struct.pack("<f", x))[0]
+
+    lines = []
+    for k in range(kmax + 1):
+        v = math.lgamma(k + 1.0)
+        hi = f32(v)
+        lo = f32(v - hi)
+        lines.append("{%sf, %sf}," % (float.hex(hi), float.hex(lo)))
+    text = "\n".join(lines) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
 
 
 def nvcc() -> str:
@@ -55,11 +78,12 @@ def _stale(obj: str, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False, jobs: int = 8) -> str:
     os.makedirs(OBJ, exist_ok=True)
+    write_lfact_table(os.path.join(OBJ, LFACT))
     cc = nvcc()
     inc = os.path.join(os.path.dirname(HERE), "include")
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "ecl.h"), __file__]
     common = [cc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-              "-I", inc, "--expt-relaxed-constexpr"]
+              "-I", inc, "-I", OBJ, "--expt-relaxed-constexpr"]
     cmds = []
     objs = []
     for src, extra in SOURCES.items():

@@ -59,6 +59,16 @@
 // stops widening once it holds the b weights the dot products use.  For the
 // near-the-money options of the workload b is about N / 2: a quarter of the
 // node updates of each pass are exact zeros that are never computed.
+// The adjoint in closed form: the level operator B' = 2p shift(B) + 2(1-p) B
+// applied N times gives every leaf j the weight 2^N C(N,j) p^j (1-p)^(N-j)
+// in the root (each path from leaf j up to the root takes j up-steps and
+// N - j down-steps), so the adjoint pass's weights, pushed back to the
+// leaves, are the binomial probabilities.  Delta and the leaf part of vega
+// are then sums over the b nonzero leaves, O(b) per option instead of the
+// adjoint lattice's O(N b): ln C(N,j) + j ln p + (N-j) ln(1-p) in pairs of
+// FP32 values (a log-factorial table generated at build time, the per-option
+// logs in FP64), then one expf.  "binomial_full" keeps the adjoint lattice
+// pass, the reference form this evaluation is tested against.
 // In FP32 emulation of this arithmetic against the FP64 oracle,
 // options of depth 1900..2048 show ~1.7e-6 relative error in the price,
 // ~0.9e-6 in delta and ~1.8e-6 in vega.
@@ -90,6 +100,46 @@ struct Lat {
 };
 
 constexpr int kRescale = 64;  // levels between rescales by 2^-64
+
+// ln k! for k = 0..2048 as (hi, lo) FP32 pairs, hi + lo = the double value
+// (generated by build.py from math.lgamma).
+__device__ const float2 g_lfact[] = {
+#include "lfact_table.inc"
+};
+
+// Pairs of FP32 values (hi, lo) with about 48 significant bits: TwoSum and
+// the FMA-based TwoProd (Dekker, Knuth), exact error-free transformations in
+// round-to-nearest.
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float2 s = two_sum(a.x, b.x);
+    const float lo = s.y + (a.y + b.y);
+    const float hi = s.x + lo;
+    return make_float2(hi, lo - (hi - s.x));
+}
+
+__device__ __forceinline__ float2 df_split(double x)
+{
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+// j * v for a small integer j (exact in FP32) and a pair v.
+__device__ __forceinline__ float2 df_scale(float j, float2 v)
+{
+    const float p = j * v.x;
+    const float e = fmaf(j, v.x, -p);
+    const float lo = fmaf(j, v.y, e);
+    const float hi = p + lo;
+    return make_float2(hi, lo - (hi - p));
+}
 
 // Lane widths (nodes per lane) the warp steps through as the lattice shrinks.
 // Going from width R to the next width R' happens when the live nodes fit in
@@ -242,11 +292,12 @@ __device__ __forceinline__ float leaf(const Opt &o, int i, float &dl, float &vg)
 }
 
 // The payoffs of leaves 0..N into the warp's shared buffer, zero beyond N.
-// Returns b, one past the last nonzero leaf (at least 1).
+// Returns b, one past the last nonzero leaf (0 when every leaf is zero): the
+// nonzero leaves are exactly 0..b-1, the priced side being out of the money.
 __device__ __forceinline__ int leaves(const Opt &o, float *sh, int lane)
 {
     __syncwarp();
-    int last = 0;
+    int last = -1;
     for (int j = lane; j <= kMaxSteps; j += kWarp) {
         float dl, vg;
         const float v = (j <= o.N) ? leaf(o, j, dl, vg) : 0.f;
@@ -414,11 +465,59 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     float d1 = 0.f;
     int shift_a = 0, rf = 0;
     const int nz = leaves(op, sh, lane);
-    const int band = p.full ? N + 1 : nz;
-    const float b = lattice(op, band, sh, lane, greeks, shift, d1, shift_a, rf);
+    const int band = p.full ? N + 1 : max(nz, 1);
+    const float b = lattice(op, band, sh, lane, greeks && p.full, shift, d1, shift_a, rf);
     if (op.refl) d1 = -d1;  // B_1 - B_0 in node order
     float delta = 0.f, vega = 0.f;
-    if (greeks) {
+    if (greeks && !p.full) {
+        // leaf j's weight pmf(j) = C(N,j) p^j (1-p)^(N-j), p = (1 + 2q)/2 with
+        // the lattice's own FP32 2q: ln pmf(j) = c0 - ln j! - ln (N-j)! + j lr,
+        // c0 = ln N! + N ln(1-p), lr = ln(p / (1-p))
+        // the per-option logs in FP64 on lane 0 only (the FP64 pipe serves two
+        // threads per clock and SM: computed by the whole warp it took 7 ms of
+        // the 2^20-option launch), then broadcast
+        float4 lg = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane == 0) {
+            const double q2o = (double)(op.refl ? -op.q2 : op.q2);
+            const double lq = log1p(-q2o);
+            const float2 lfn = g_lfact[N];
+            const float2 a = df_split(log1p(q2o) - lq);
+            const float2 b = df_split((double)lfn.x + (double)lfn.y + (double)N * (lq - 0.69314718055994530942));
+            lg = make_float4(a.x, a.y, b.x, b.y);
+        }
+        const float2 lr = make_float2(__shfl_sync(kFull, lg.x, 0), __shfl_sync(kFull, lg.y, 0));
+        const float2 c0 = make_float2(__shfl_sync(kFull, lg.z, 0), __shfl_sync(kFull, lg.w, 0));
+        // leaf j in the money (exactly the first nz stored leaves): dS_T/dS =
+        // g, dS_T/dsigma = S g m sqrt(dt) with g = e^(a m), m = 2j - N (both
+        // negated on the put side), so one exponential ln pmf(j) + a m gives
+        // the weighted g of both sums
+        float sd = 0.f, sv = 0.f;
+#pragma unroll 2
+        for (int i = lane; i < nz; i += kWarp) {
+            const int j = op.refl ? N - i : i;
+            const float m = (float)(2 * j - N);
+            const float2 a = g_lfact[j], c = g_lfact[N - j];
+            float2 l = df_add(c0, make_float2(-a.x, -a.y));
+            l = df_add(l, make_float2(-c.x, -c.y));
+            l = df_add(l, df_scale((float)j, lr));
+            const float am = op.a * m;
+            l = df_add(l, make_float2(am, fmaf(op.a, m, -am)));
+            const float e = expf(l.x);
+            const float wg = fmaf(e, l.y, e);
+            sd += wg;
+            sv = fmaf(wg, m, sv);
+        }
+        const float sgn = op.put ? -1.f : 1.f;
+        sd *= sgn;
+        sv *= sgn * S * sdt;
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            sd += __shfl_xor_sync(kFull, sd, o2);
+            sv += __shfl_xor_sync(kFull, sv, o2);
+        }
+        delta = sd;
+        vega = sv;
+    } else if (greeks) {
         const int top = kWarp * rf - 1;  // node j of level N - 1 at shared node top - j
         // leaf derivatives pushed back one level (x'_j from x_j, x_{j+1}),
         // dotted with A; the leaves are evaluated again here rather than kept
@@ -449,7 +548,9 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
         if (op.put) price += S - K * disc;
         p.price[o] = price;
         if (greeks) {
-            const float scale_a = ldexpf(disc, -shift_a);
+            // the closed-form weights are probabilities; the lattice's adjoint
+            // weights carry 2^shift_a
+            const float scale_a = p.full ? ldexpf(disc, -shift_a) : disc;
             const float q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));  // 2 dq/dsigma
             delta *= scale_a;
             if (op.put) delta += 1.0f;

@@ -83,3 +83,44 @@ def test_the_q_term_is_needed(oracle_mod):
         assert abs(vl + vq - V[i]) <= 1e-9 * max(abs(V[i]), 1e-4 * float(o["S"][i]))
         misses.append(abs(vl - V[i]) / max(abs(V[i]), 1e-4 * float(o["S"][i])))
     assert min(misses) > 1e-3
+
+
+def test_closed_form_leaf_weights_give_the_oracle_delta_and_vega(oracle_mod):
+    # The adjoint of N levels of B' = 2p shift(B) + 2(1-p) B is, at the leaves,
+    # 2^N times the binomial probabilities C(N,j) p^j (1-p)^(N-j) (the paths
+    # from leaf j to the root), so delta and the vega leaf part are
+    # probability-weighted sums of the leaf derivatives.  Restated in numpy
+    # in log space from math.lgamma, against the oracle's dual numbers; a
+    # weight taken from the wrong end of the lattice (pmf(N - j)) fails.
+    o = W.binomial_options(48, seed=77, min_steps=1, max_steps=2048)
+    rp, rd, rv = oracle_mod.binomial(o["S"], o["K"], o["T"], o["sigma"], o["steps"], o["r"])
+    r = o["r"]
+    for k in range(48):
+        S, K, T, sg = (float(o[x][k]) for x in ("S", "K", "T", "sigma"))
+        N = int(o["steps"][k])
+        dt = T / N
+        sdt = math.sqrt(dt)
+        a = sg * sdt
+        q = (math.expm1(r * dt) - 2.0 * math.sinh(0.5 * a) ** 2) / (2.0 * math.sinh(a))
+        p = 0.5 + q
+        j = np.arange(N + 1)
+        m = 2.0 * j - N
+        g = np.exp(a * m)
+        ST = S * g
+        lpmf = np.array([math.lgamma(N + 1) - math.lgamma(i + 1) - math.lgamma(N - i + 1) for i in j])
+        pmf = np.exp(lpmf + j * math.log(p) + (N - j) * math.log1p(-p))
+        disc = math.exp(-r * T)
+        put = S > K
+        itm = (ST < K) if put else (ST > K)
+        sgn = -1.0 if put else 1.0
+        delta = disc * (pmf * np.where(itm, sgn * g, 0.0)).sum() + (1.0 if put else 0.0)
+        # vega = leaf part + the q term (the lattice's dependence on sigma through p)
+        qp = sdt * (-0.5 - q * math.cosh(a) / math.sinh(a))  # dq/dsigma
+        dpmf = pmf * (j / p - (N - j) / (1.0 - p)) * qp
+        pay = np.where(itm, sgn * (ST - K), 0.0)
+        vega = disc * ((pmf * np.where(itm, sgn * ST * m * sdt, 0.0)).sum() + (dpmf * pay).sum())
+        assert abs(delta - rd[k]) <= 1e-9 * max(abs(rd[k]), 1e-4), (k, delta, rd[k])
+        assert abs(vega - rv[k]) <= 1e-9 * max(abs(rv[k]), 1e-4 * S), (k, vega, rv[k])
+        wrong = disc * (pmf[::-1] * np.where(itm, sgn * g, 0.0)).sum() + (1.0 if put else 0.0)
+        if abs(2 * q) > 1e-3:
+            assert abs(wrong - rd[k]) > 1e-6 * max(abs(rd[k]), 1e-4)

@@ -112,11 +112,12 @@ def test_config4_full_batch_sampled(E, oracle_mod):
 
 
 def test_banded_lattice_matches_the_full_lattice(E):
-    # The banded program skips nodes that are exactly zero and stores the
-    # call lattice reflected; the full program computes every node in node
-    # order.  Prices agree bit for bit; greeks agree bit for bit for the puts
-    # (in-the-money calls) and up to the summation order of the dot products
-    # for the calls.  Every width boundary, the extremes, then a random batch.
+    # The banded program skips nodes that are exactly zero, stores the call
+    # lattice reflected and takes its greeks from closed-form adjoint
+    # weights; the full program computes every node in node order and runs
+    # the adjoint lattice.  Prices agree bit for bit; the two greeks
+    # evaluations (each within ~1e-6 of the exact values) agree to 5e-6.
+    # Every width boundary, the extremes, then a random batch.
     widths = [1, 2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64]
     steps = sorted({v for w in widths for v in (32 * w - 1, 32 * w, 32 * w + 1) if 1 <= v <= 2048} | {1, 2, 3})
     o = W.binomial_options(len(steps), seed=44)
@@ -127,10 +128,8 @@ def test_banded_lattice_matches_the_full_lattice(E):
             pf, gf, _ = run_bino(E, opts, greeks, kernel="binomial_full")
             assert np.array_equal(pb.view(np.uint32), pf.view(np.uint32))
             if greeks:
-                put = opts["S"] > opts["K"]
-                assert np.array_equal(gb[put].view(np.uint32), gf[put].view(np.uint32))
-                scale = np.maximum(np.abs(gf), np.array([1e-4, 1e-4]) * opts["S"][:, None])
-                assert (np.abs(gb - gf) <= 1e-6 * scale).all()
+                scale = np.maximum(np.abs(gf), np.stack([np.full(len(gf), 1e-4), 1e-4 * opts["S"]], 1))
+                assert (np.abs(gb - gf) <= 5e-6 * scale).all(), (np.abs(gb - gf) / scale).max()
 
 
 def test_deep_out_of_the_money_band_of_one_leaf(E, oracle_mod):
