@@ -66,8 +66,9 @@
 // leaves, are the binomial probabilities.  Delta and the leaf part of vega
 // are then sums over the b nonzero leaves, O(b) per option instead of the
 // adjoint lattice's O(N b): ln C(N,j) + j ln p + (N-j) ln(1-p) in pairs of
-// FP32 values (a log-factorial table generated at build time, the per-option
-// logs in FP64), then one expf.  "binomial_full" keeps the adjoint lattice
+// FP32 values (a log-factorial table generated at build time, the
+// per-option logs from their series, in FP64 on coarse lattices), then one
+// expf.  "binomial_full" keeps the adjoint lattice
 // pass, the reference form this evaluation is tested against.
 // In FP32 emulation of this arithmetic against the FP64 oracle,
 // options of depth 1900..2048 show ~1.7e-6 relative error in the price,
@@ -141,6 +142,24 @@ __device__ __forceinline__ float2 df_scale(float j, float2 v)
     return make_float2(hi, lo - (hi - p));
 }
 
+// ln(1 + x) as a pair for |x| <= 1/4 from the Mercator series
+//   ln(1 + x) = x - x^2/2 + x^3 (1/3 - x/4 + x^2/5 - ...):
+// x - x^2/2 carried exactly (TwoProd of x*x), the cubic tail (below
+// 0.03 |x|) in FP32 with 16 terms, the rest below |x|^19 / 19.
+__device__ __forceinline__ float2 df_log1p(float x)
+{
+    float t = 1.0f / 18.0f;
+#pragma unroll
+    for (int k = 17; k >= 3; --k) t = fmaf(t, -x, 1.0f / (float)k);
+    const float x2 = x * x;
+    const float x2e = fmaf(x, x, -x2);
+    const float tail = x2 * x * t;
+    const float2 s = two_sum(x, -0.5f * x2);
+    const float lo = s.y + fmaf(-0.5f, x2e, tail);
+    const float hi = s.x + lo;
+    return make_float2(hi, lo - (hi - s.x));
+}
+
 // Lane widths (nodes per lane) the warp steps through as the lattice shrinks.
 // Going from width R to the next width R' happens when the live nodes fit in
 // 32 R'.  Every width is a fully unrolled level loop plus a repack, so the
@@ -206,8 +225,21 @@ __device__ __forceinline__ void levels(float (&B)[kMaxR], Lat &L, float *sh, int
     // in runs up to the next rescale (every kRescale levels, by 2^-kRescale: exact)
     while (n > 0) {
         const int m = min(n, kRescale - L.rescale);
+        // two levels per iteration at the narrow widths, where the loop's
+        // compare and branch are a larger share of a level (measured: 1-2%
+        // faster; at widths up to 32 the larger code ran 10% slower)
+        if constexpr (R <= 16) {
+            int i = 0;
 #pragma unroll 1
-        for (int i = 0; i < m; ++i) level<R>(B, L.q2, src, top);
+            for (; i + 2 <= m; i += 2) {
+                level<R>(B, L.q2, src, top);
+                level<R>(B, L.q2, src, top);
+            }
+            if (i < m) level<R>(B, L.q2, src, top);
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < m; ++i) level<R>(B, L.q2, src, top);
+        }
         n -= m;
         L.rescale += m;
         if (L.rescale == kRescale) {
@@ -470,46 +502,53 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     if (op.refl) d1 = -d1;  // B_1 - B_0 in node order
     float delta = 0.f, vega = 0.f;
     if (greeks && !p.full) {
-        // leaf j's weight pmf(j) = C(N,j) p^j (1-p)^(N-j), p = (1 + 2q)/2 with
-        // the lattice's own FP32 2q: ln pmf(j) = c0 - ln j! - ln (N-j)! + j lr,
-        // c0 = ln N! + N ln(1-p), lr = ln(p / (1-p))
-        // the per-option logs in FP64 on lane 0 only (the FP64 pipe serves two
-        // threads per clock and SM: computed by the whole warp it took 7 ms of
-        // the 2^20-option launch), then broadcast
-        float4 lg = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane == 0) {
-            const double q2o = (double)(op.refl ? -op.q2 : op.q2);
-            const double lq = log1p(-q2o);
+        // stored leaf i's weight in the root is the binomial pmf
+        // C(N,i) w^i (1-w)^(N-i), w = (1 + v)/2 with v the lattice's own FP32
+        // 2q in storage order (negated when reflected); its exponential g =
+        // e^(a m), m = 2j - N = s (2i - N) (s = -1 when reflected), is folded
+        // into the same logarithm:
+        //   ln(pmf g) = C - ln i! - ln (N-i)! + i L,
+        //   C = ln N! + N ln((1-v)/2) - s a N,  L = ln((1+v)/(1-v)) + 2 s a
+        const float v = op.q2;
+        const float sa = op.refl ? -op.a : op.a;
+        float2 C, L;
+        if (fabsf(v) <= 0.25f) {
+            // FP32 pairs from the series (all lanes alike: no FP64)
+            const float2 lp = df_log1p(v), lm = df_log1p(-v);
+            constexpr float kLn2Hi = 0.693147182464599609375f;  // ln 2 = hi + lo
+            constexpr float kLn2Lo = (float)(0.69314718055994530942 - 0.693147182464599609375);
+            const float2 lh = df_add(lm, make_float2(-kLn2Hi, -kLn2Lo));
+            const float na = (float)N * sa;
+            C = df_add(g_lfact[N], df_scale((float)N, lh));
+            C = df_add(C, make_float2(-na, -fmaf((float)N, sa, -na)));
+            L = df_add(df_add(lp, make_float2(-lm.x, -lm.y)), make_float2(2.0f * sa, 0.f));
+        } else {
+            // coarse lattices (|2q| > 1/4, a few steps): FP64 logs (no
+            // shuffle here: a warp-synchronous call under this branch made
+            // the compiler treat the whole kernel as divergent, +7%)
+            const double lq = log1p(-(double)v);
             const float2 lfn = g_lfact[N];
-            const float2 a = df_split(log1p(q2o) - lq);
-            const float2 b = df_split((double)lfn.x + (double)lfn.y + (double)N * (lq - 0.69314718055994530942));
-            lg = make_float4(a.x, a.y, b.x, b.y);
+            L = df_split(log1p((double)v) - lq + 2.0 * (double)sa);
+            C = df_split((double)lfn.x + (double)lfn.y + (double)N * (lq - 0.69314718055994530942 - (double)sa));
         }
-        const float2 lr = make_float2(__shfl_sync(kFull, lg.x, 0), __shfl_sync(kFull, lg.y, 0));
-        const float2 c0 = make_float2(__shfl_sync(kFull, lg.z, 0), __shfl_sync(kFull, lg.w, 0));
-        // leaf j in the money (exactly the first nz stored leaves): dS_T/dS =
-        // g, dS_T/dsigma = S g m sqrt(dt) with g = e^(a m), m = 2j - N (both
-        // negated on the put side), so one exponential ln pmf(j) + a m gives
-        // the weighted g of both sums
+        // leaf in the money (exactly the first nz stored leaves): dS_T/dS =
+        // g, dS_T/dsigma = S g m sqrt(dt) (both negated on the put side), so
+        // one exponential gives the weighted g of both sums
         float sd = 0.f, sv = 0.f;
 #pragma unroll 2
         for (int i = lane; i < nz; i += kWarp) {
-            const int j = op.refl ? N - i : i;
-            const float m = (float)(2 * j - N);
-            const float2 a = g_lfact[j], c = g_lfact[N - j];
-            float2 l = df_add(c0, make_float2(-a.x, -a.y));
-            l = df_add(l, make_float2(-c.x, -c.y));
-            l = df_add(l, df_scale((float)j, lr));
-            const float am = op.a * m;
-            l = df_add(l, make_float2(am, fmaf(op.a, m, -am)));
+            const float2 x = g_lfact[i], y = g_lfact[N - i];
+            float2 l = df_add(C, make_float2(-x.x, -x.y));
+            l = df_add(l, make_float2(-y.x, -y.y));
+            l = df_add(l, df_scale((float)i, L));
             const float e = expf(l.x);
             const float wg = fmaf(e, l.y, e);
             sd += wg;
-            sv = fmaf(wg, m, sv);
+            sv = fmaf(wg, (float)(2 * i - N), sv);
         }
         const float sgn = op.put ? -1.f : 1.f;
         sd *= sgn;
-        sv *= sgn * S * sdt;
+        sv *= (op.refl ? -sgn : sgn) * S * sdt;
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
             sd += __shfl_xor_sync(kFull, sd, o2);
