@@ -43,7 +43,9 @@ LFACT = "lfact_table.inc"  # generated into _build: ln k! for k = 0..2048 as FP3
 def write_lfact_table(path: str, kmax: int = 2048) -> None:
     """ln k! (math.lgamma(k + 1), double precision) split into two FP32
     values hi + lo, written as C hex-float initialisers for the binomial
-    kernel's closed-form leaf weights."""
+    kernel's closed-form leaf weights.  hi is the value rounded to a multiple
+    of 2^-10 (below 2^14 for k <= 2048, so exact in FP32), so that sums of hi
+    parts are exact in FP32; lo (at most 2^-11) is the FP32 remainder."""
     import math
     import struct
 
@@ -53,7 +55,8 @@ def write_lfact_table(path: str, kmax: int = 2048) -> None:
     lines = []
     for k in range(kmax + 1):
         v = math.lgamma(k + 1.0)
-        hi = f32(v)
+        hi = round(v * 1024.0) / 1024.0
+        assert f32(hi) == hi and abs(hi) < 2.0 ** 14
         lo = f32(v - hi)
         lines.append("{%sf, %sf}," % (float.hex(hi), float.hex(lo)))
     text = "\n".join(lines) + "\n"
