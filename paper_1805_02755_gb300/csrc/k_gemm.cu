@@ -2,9 +2,12 @@
 //
 //   C[M x N] (FP32, row-major) = A[M x K] (bf16, row-major) * Bt[N x K]^T
 //
-// The NDRange is the grid of 128 x 256 output tiles in row-major tile order;
-// one work-group = one tile, and the scheduling unit is one row of tiles, so
-// Static / Dynamic / HGuided hand out packages of whole 128-row tiles.
+// The NDRange is the grid of 128 x 256 output tiles, numbered in column
+// groups (tc::tile_at: the tiles of W tile columns row by row, then the next
+// W columns), so that a wave of concurrent tiles reads few strips of A and
+// Bt; one work-group = one tile, and the scheduling unit is as many tiles as a
+// tile row holds, so Static / Dynamic / HGuided hand out packages of whole
+// grains of that size.
 //
 // Each persistent CTA (192 threads, one per SM) is warp-specialised:
 //   warp 0    claims chunks (tiles) from the package queue and feeds a ring
@@ -72,6 +75,7 @@ struct GemmParams {
     float *C;
     int64_t M, N, K;
     int64_t tiles_n;
+    tc::TileOrder order;  // work-group id -> output tile
     uint32_t kblocks;   // K slices per sweep
     uint32_t sweeps;    // 1 (bf16) or 3 (split)
 };
@@ -158,8 +162,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     sm.ring_nch[r] = c.nchunks;
                     mbar_arrive(&sm.rfull[r]);
                     ++ri;
-                    const int m0 = (int)((tile / p.tiles_n) * BM);
-                    const int n0 = (int)((tile % p.tiles_n) * BN);
+                    int64_t mt, nt;
+                    tc::tile_at(p.order, tile, mt, nt);
+                    const int m0 = (int)(mt * BM);
+                    const int n0 = (int)(nt * BN);
                     for (uint32_t k = 0; k < ksteps; ++k, ++kq) {
                         const uint32_t st = kq % NSTAGE;
                         if (!mbar_wait(&sm.empty[st], ((kq / NSTAGE) & 1) ^ 1, err, gerr)) break;
@@ -261,8 +267,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            const int64_t m = (tile / p.tiles_n) * BM + quarter * 32 + lane;
-            const int64_t n0 = (tile % p.tiles_n) * BN;
+            int64_t mt, nt;
+            tc::tile_at(p.order, tile, mt, nt);
+            const int64_t m = mt * BM + quarter * 32 + lane;
+            const int64_t n0 = nt * BN;
             const bool vec = (p.N % 4) == 0;
 #pragma unroll 1
             for (int cc = 0; cc < BN / 32; ++cc) {
@@ -442,6 +450,7 @@ ecl_status launch_main(const Maps &maps, const KArgs &a, const SchedArgs &s, con
     p.tiles_n = (p.N + BN - 1) / BN;
     p.kblocks = (uint32_t)((p.K + BK - 1) / BK);
     p.sweeps = sweeps;
+    p.order = tile_order((p.M + BM - 1) / BM, p.tiles_n, c.grid, (double)BM, (double)BN);  // strips of equal K
     k_gemm<<<c.grid, NTHREADS, SMEM_BYTES, c.stream>>>(maps, p, s);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {

@@ -21,8 +21,9 @@
 // two cross buffers let one tile's epilogue overlap the next tile.  TMEM
 // columns: hh[0], hh[1], cross[0], cross[1], 128 each (512 in total).
 //
-// Tiles are 128 x 128 (one work-group each); the scheduling unit is a row
-// of tiles.  Each persistent CTA (192 threads, one per SM):
+// Tiles are 128 x 128 (one work-group each), numbered in column groups as
+// in the plain GEMM; the scheduling unit is as many tiles as a tile row
+// holds.  Each persistent CTA (192 threads, one per SM):
 //   warp 0    claims tiles and issues the TMA loads of the six operand
 //             pieces (A and Bt: h, m, l) of each 64-wide K slice into a
 //             2-stage ring (96 KB per stage);
@@ -76,6 +77,7 @@ struct Gemm6Params {
     float *C;
     int64_t M, N, K;
     int64_t tiles_n;
+    tc::TileOrder order;  // work-group id -> output tile
     uint32_t kblocks;   // K slices of 64
     uint32_t chunk_kb;  // K slices per hh chunk
 };
@@ -165,8 +167,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     sm.ring_nch[r] = c.nchunks;
                     mbar_arrive(&sm.rfull[r]);
                     ++ri;
-                    const int m0 = (int)((tile / p.tiles_n) * BM);
-                    const int n0 = (int)((tile % p.tiles_n) * BN);
+                    int64_t mt, nt;
+                    tc::tile_at(p.order, tile, mt, nt);
+                    const int m0 = (int)(mt * BM);
+                    const int n0 = (int)(nt * BN);
                     for (uint32_t k = 0; k < p.kblocks; ++k, ++kq) {
                         const uint32_t st = kq % NST;
                         if (!mbar_wait(&sm.empty[st], ((kq / NST) & 1) ^ 1, err, gerr)) break;
@@ -309,8 +313,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            const int64_t m = (tile / p.tiles_n) * BM + quarter * 32 + lane;
-            const int64_t n0 = (tile % p.tiles_n) * BN;
+            int64_t mt, nt;
+            tc::tile_at(p.order, tile, mt, nt);
+            const int64_t m = mt * BM + quarter * 32 + lane;
+            const int64_t n0 = nt * BN;
             const bool vec = (p.N % 4) == 0;
 #pragma unroll
             for (int cc = 0; cc < BN / 32; ++cc) {
@@ -479,6 +485,7 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.K = K;
     p.tiles_n = (N + BN - 1) / BN;
     p.kblocks = (uint32_t)((K + BK - 1) / BK);
+    p.order = tc::tile_order((M + BM - 1) / BM, p.tiles_n, c.grid, (double)BM, (double)BN);  // strips of equal K
     const int32_t ck = a.i32(6);
     p.chunk_kb = ck > 0 ? (uint32_t)ck : 1u;
     if (p.chunk_kb > p.kblocks) p.chunk_kb = p.kblocks;

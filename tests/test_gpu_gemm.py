@@ -67,8 +67,10 @@ def absab(A, Bt, O):
     return a @ b.T
 
 
+# (300, 2600, 1000): 11 tile columns in column groups of 9 and 2 with 152
+# CTAs, so the tile order's narrower last group is exercised
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 128), (200, 300, 136), (1, 1, 8), (129, 257, 1000),
-                                   (512, 256, 2048)])
+                                   (512, 256, 2048), (300, 2600, 1000)])
 def test_bf16_shapes(E, oracle_mod, M, N, K):
     A, Bt = W.gemm_matrices(M, N, K, seed=500 + M + N + K)
     got, _ = run_gemm(E, A, Bt)

@@ -52,7 +52,9 @@ def absab(A, Bt):
     return np.abs(A.astype(np.float64)) @ np.abs(Bt.astype(np.float64)).T
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 300, 136), (1, 1, 8), (129, 257, 1000), (256, 384, 2048)])
+# (300, 2000, 1000): 16 tile columns in column groups of 12 and 4 with 152 CTAs
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 300, 136), (1, 1, 8), (129, 257, 1000), (256, 384, 2048),
+                                   (300, 2000, 1000)])
 def test_split6_shapes(E, oracle_mod, M, N, K):
     A, Bt = W.gemm_matrices(M, N, K, seed=900 + M + N + K)
     got, _ = run_gemm6(E, A, Bt)
