@@ -58,7 +58,7 @@ EXTRA_PROGRAMS = {"gemm_split6"}
 
 # ncu-measured DRAM bytes per launch of the dominant kernel (null once the kernel changes)
 NCU_TRAFFIC = {
-    "binomial": {"bytes_per_launch": 488.448e3 * 64,
+    "binomial": {"bytes_per_launch": 756.224e3 * 64,
                  "source": "profiles/binomial_greeks_16384_options.md (16384 options x 64; reads, the results "
                            "stay in L2 within the capture)"},
 }
@@ -478,13 +478,13 @@ class Binomial(Workload):
                     batched_over_plain=ms_batched / ms_plain)
 
     def after(self):
-        # FP32 instructions per node update of the backward induction: 3 (add,
-        # sub, FMA; flops with FMA = 2: 4), over the nodes that can be nonzero
+        # FP32 instructions per node update of the backward induction: 2 (add,
+        # FMA; flops with FMA = 2: 3), over the nodes that can be nonzero
         # (its band).  Delta and the vega leaf part are sums over the nonzero
         # leaves with closed-form adjoint weights, O(b) per option, not counted
         # (conservative).  The full lattice's node count is reported beside it.
         nb = self.nodes_price
-        return dict(bound="alu", inst=3.0 * nb, flops=4.0 * nb, unit_name="options/s",
+        return dict(bound="alu", inst=2.0 * nb, flops=3.0 * nb, unit_name="options/s",
                     units=self.n, extra={"node_updates_per_s": nb,
                                          "full_lattice_node_updates_per_s": self.nodes,
                                          "greeks_leaf_terms_per_s": self.greeks_terms})

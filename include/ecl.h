@@ -411,14 +411,19 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *     4 B steps int32[n] (1..2048; other depths give NaN)  5 S float r  6 S int32 n
  *     7 B price float[n]  8 B greeks float2[n] (delta, vega) or NULL
  *   European call on a Cox-Ross-Rubinstein lattice of steps[o] steps,
- *   backward induction in FP32 by one warp per option; with greeks the
- *   exact derivatives of the lattice price with respect to S and sigma
- *   (one adjoint pass of the lattice).  Nodes that are exactly zero (below
- *   the strike on the out-of-the-money side) are not computed.
+ *   backward induction in FP32 by one warp per option (two FP32
+ *   instructions per node); with greeks the exact derivatives of the
+ *   lattice price with respect to S and sigma, from the lattice's adjoint
+ *   weights in closed form (binomial probabilities).  Nodes that are
+ *   exactly zero (below the strike on the out-of-the-money side) are not
+ *   computed.  Inputs: S, K > 0 and T, sigma >= 0; an option whose
+ *   out-of-the-money leaves are more than N/2 + 1 (only with sigma or T
+ *   negative) gets NaN results.
  *
  * "binomial_full"  (the arguments of "binomial")  the same prices computing
  *   every node of every level: the reference form of "binomial" (identical
- *   prices; greeks equal up to the summation order of their dot products).
+ *   prices; greeks from the adjoint lattice, within ~1e-6 of the closed
+ *   form).
  *
  * "binomial_batch"  (4 args, out pattern 1:32, lws 32)  many option batches
  *   of uneven size in one NDRange and one persistent launch:
@@ -426,7 +431,7 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *     1 S int32 count  2 S int64 total options  3 S int32 with_greeks
  *   instance i prices options [first_i, first_i + n_i) of the NDRange (first
  *   ascending from 0, sum of n_i = total) from its own arrays; with_greeks = 0
- *   skips the delta/vega lattices for the whole batch.  The engine does not
+ *   skips delta and vega for the whole batch.  The engine does not
  *   see the arrays the table points to: the caller guarantees them.
  *
  * "mandelbrot_batch"  (3 args, one output pixel block per work-item, lws

@@ -5,9 +5,9 @@
   "nbody_adjoint" program: dL/dpos4 = dL/dE * (dE/dr_i, dE/dm_i).
 * ``binomial_price(S, K, T, sigma, steps, r)``: CRR call prices (the
   "binomial" program).  When S or sigma requires a gradient the forward launch
-  also computes delta and vega (one adjoint pass of the lattice after the
-  backward induction: delta and the leaf part of vega are dot products of the
-  adjoint weights with the leaf derivatives), and
+  also computes delta and vega (the lattice's adjoint weights in closed form,
+  binomial probabilities: delta and the leaf part of vega are sums of those
+  weights times the leaf derivatives over the nonzero leaves), and
   backward returns dL/dS = dL/dV * delta, dL/dsigma = dL/dV * vega.  K, T and
   r get no gradient.
 

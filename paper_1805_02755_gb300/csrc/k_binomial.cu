@@ -15,21 +15,29 @@
 // Arithmetic (exact in real numbers, arranged for FP32):
 //   p = 1/2 + q,  q = (expm1(r dt) - 2 sinh^2(a/2)) / (2 sinh a),  a = sigma sqrt(dt)
 // is the CRR probability (e^{r dt} - d)/(u - d) written so that the large
-// part 1/2 is exact and only the small q carries rounding.  The lattice is
-// stored scaled by 2 per level, B = 2^(N-t) V / disc^(N-t), so one node
-// update is  B_j <- (B_{j+1} + B_j) + 2q (B_{j+1} - B_j)  (add, sub, FMA);
-// the power of two is removed at the end together with disc^N = e^{-rT}.
-// Every 64 levels all nodes are multiplied by 2^-64 (exact); leaves stay
-// below ~1e16 (S = 100, sigma = 0.5, T = 2, N = 2048), so the scaled lattice
-// stays below ~2e35, inside the FP32 range.
+// part 1/2 is exact and only the small q carries rounding.  With v = 2q the
+// level is V'_j = disc (p V_{j+1} + (1 - p) V_j); divided by disc (1 - p)
+// per level it becomes
+//   C'_j = C_j + rho C_{j+1},  rho = p / (1 - p) = 1 + eta,  eta = 2v / (1 - v),
+// and one node update is  C_j <- fma(eta, C_{j+1}, C_{j+1} + C_j)  (add,
+// FMA): the coefficient 1 is exact and only the small eta carries rounding,
+// so the lattice is that of a probability within ~1e-9 of p.  The root is
+// the price times (2 + eta)^N / disc^N; the factor is removed at the end
+// from its logarithm in pairs of FP32 values.  The largest node grows by at
+// most 2 + eta per level, so every K levels (K = 64, fewer when eta > 0:
+// K log2(2 + eta) <= 64) all nodes are multiplied by 2^-E, E = the ceiling
+// of K log2(2 + eta) (exact); leaves stay below ~1e16 (S = 100,
+// sigma = 0.5, T = 2, N = 2048), so the lattice stays below ~2e35, inside
+// the FP32 range.
 // In-the-money calls (S > K) are priced through the put on the same lattice
 // and put-call parity, which holds exactly on a CRR lattice:
 //   C = P + S - K e^{-rT},  dC/dS = dP/dS + 1,  dC/dsigma = dP/dsigma.
 // The put lattice of a deep in-the-money call holds small values, while the
 // call lattice would carry two large vega terms (leaf and dq/dsigma parts)
 // that cancel, losing several digits in FP32.
-// Greeks are the exact derivatives of this discrete price.  Forward mode
-// through one level gives
+// Greeks are the exact derivatives of this discrete price.  In terms of the
+// lattice scaled by 2 / disc per level, B'_j = (1 + v) B_{j+1} + (1 - v) B_j
+// (B = (1 - v)^k C after k levels), forward mode through one level gives
 //   delta tree: the same recursion, leaves u^j d^(N-j) for in-the-money leaves;
 //   vega tree:  dB_j <- (dB_{j+1} + dB_j) + 2q (dB_{j+1} - dB_j) + 2q' (B_{j+1} - B_j),
 //               q' = dq/dsigma = sqrt(dt) (-1/2 - q coth a),
@@ -41,7 +49,7 @@
 // So delta and the leaf part of vega are the same recursion applied to the
 // leaf derivatives, linear functionals of the leaves.  One reverse (adjoint)
 // pass gives the weights A of every node of level N - 1 in the root
-// (A = 1 at the root, A'_j = (A_j + A_{j-1}) + 2q (A_{j-1} - A_j) outwards),
+// (A = 1 at the root, A'_j = A_j + rho A_{j-1} outwards on the C lattice),
 // and both become dot products of A with the leaf derivatives pushed back
 // one level; with B_1 - B_0 kept from the price pass,
 //   vega = <A, vega leaves'> + N 2q' (B_1 - B_0).
@@ -51,9 +59,8 @@
 // Only the out-of-the-money side is priced, so its nonzero leaves form one
 // contiguous run: j < b for the put, j > N - b for the call.  The call's
 // lattice is stored reflected (node j at index N - j), where its level is
-// the same operator with -2q in place of 2q (bit for bit: the difference
-// changes sign exactly, the sum commutes), so both sides have their
-// nonzero leaves at indices 0 .. b - 1.  Nodes at index >= b stay exactly
+// the same operator with v = -2q in place of 2q (and eta from that v), so
+// both sides have their nonzero leaves at indices 0 .. b - 1.  Nodes at index >= b stay exactly
 // zero while the lattice is wider than b, so the backward induction runs at
 // the width that holds min(t + 1, b) nodes of level t, and the adjoint pass
 // stops widening once it holds the b weights the dot products use.  For the
@@ -91,16 +98,18 @@ struct BinoParams {
     int64_t n;
     float *price;
     float2 *greeks;  // (delta, vega) or nullptr
-    int full;        // 1: compute every node (the reference form of the banded lattice)
 };
 
 struct Lat {
-    float q2;      // 2q (-2q on the reflected lattice)
+    float eta;     // level coefficient: C'_i = C_i + (1 + eta) C_{i+1} (storage order)
+    float f;       // 2^-E, one rescale
+    int K;         // levels between rescales
+    int E;
     int rescale;   // levels since the last rescale
     int shift;     // power of two still to remove from the result
 };
 
-constexpr int kRescale = 64;  // levels between rescales by 2^-64
+constexpr int kRescale = 64;  // at most 64 levels (growth at most 2^64) between rescales
 
 // ln k! for k = 0..2048 as (hi, lo) FP32 pairs, hi + lo = the double value
 // (generated by build.py from math.lgamma).
@@ -172,33 +181,42 @@ constexpr int kNWidths = sizeof(kWidths) / sizeof(kWidths[0]);
 __host__ __device__ constexpr int width_at(int i) { return i < kNWidths ? kWidths[i] : 0; }
 constexpr int kMaxR = 64;
 constexpr int kMaxSteps = kWarp * kMaxR;               // deepest lattice: 2048 steps
+// The banded lattice starts at width 40: its band, the out-of-the-money
+// side's nonzero leaves, holds at most N/2 + 1 <= 1025 nodes (for sigma,
+// T >= 0), so it never needs the three widest widths, which only the full
+// lattice (up to 2049 leaves) runs.  Its level code and its registers stop
+// at 40 slots per lane.
+constexpr int kW0Band = 3;
+static_assert(width_at(kW0Band) == 40, "banded lattice starts at width 40");
 constexpr int kShNodes = kMaxSteps + 1 + kMaxSteps / 32 + 32;  // leaves 0..N with padding
 
-// Resident one-warp CTAs per SM the register budget is set for (255
-// registers a thread).  Measured on the 2^20-option batch with greeks:
-// 8 -> 193.5 ms; 12 (168 registers) 250 ms, 16 (128) 286 ms, 20 (96, with
-// spills) 309 ms: a tighter budget costs the level loops more than the extra
-// warps win back.
-constexpr int kMinCtas = 8;
+// Resident one-warp CTAs per SM the register budget is set for.  A node
+// update is an add and an FMA that depends on it, so a warp waits on its own
+// FP32 latency unless the scheduler has other warps: the banded lattice (at
+// most 40 slots a lane, inlined) runs at 16 per SM (128 registers, no
+// spills).  Measured on the 2^20-option batch with greeks: 8 per SM 63.8 ms,
+// 10 61.3, 12 51.4, 16 49.4, 20 (96 registers, spills) 51.9.  The full
+// lattice (64 slots a lane) keeps 8 (255 registers).
+constexpr int kMinCtas = 16;
+constexpr int kMinCtasFull = 8;
 
 __device__ __forceinline__ int shidx(int j) { return j + (j >> 5); }  // avoids bank conflicts
 
-// One level of the recursion B'_k = (B_k + B_{k+1}) + 2q (B_{k+1} - B_k) on
-// the first R slots of every lane (lane l holds nodes l*R .. l*R + R - 1).
-// The last lane's last slot takes zero as its upper neighbour: above the
-// top of the backward induction (a dead slot), above the nonzero band of a
-// lattice wider than the band (which keeps the nodes there at zero), and
-// the not-yet-reached node before node 0 in the adjoint (stored reversed).
+// One level of the recursion C'_k = C_k + (1 + eta) C_{k+1} on the first R
+// slots of every lane (lane l holds nodes l*R .. l*R + R - 1), two FP32
+// instructions per node.  The last lane's last slot has zero above it: the
+// node above the top of the backward induction (a dead slot), above the
+// nonzero band of a lattice wider than the band (which keeps the nodes
+// there at zero), and the not-yet-reached node before node 0 in the adjoint
+// (stored reversed).  With a zero neighbour the update leaves a node as it
+// is (fma(eta, 0, 0 + x) = x exactly), so that lane skips it.
 template <int R>
-__device__ __forceinline__ void level(float (&B)[kMaxR], float q2, int src, bool top)
+__device__ __forceinline__ void level(float (&B)[kMaxR], float eta, int src, bool top)
 {
-    float bn = __shfl_sync(kFull, B[0], src);
-    if (top) bn = 0.f;
+    const float bn = __shfl_sync(kFull, B[0], src);
 #pragma unroll
-    for (int s = 0; s < R; ++s) {
-        const float up = (s + 1 < R) ? B[s + 1] : bn;
-        B[s] = fmaf(q2, up - B[s], up + B[s]);
-    }
+    for (int s = 0; s + 1 < R; ++s) B[s] = fmaf(eta, B[s + 1], B[s + 1] + B[s]);
+    if (!top) B[R - 1] = fmaf(eta, bn, bn + B[R - 1]);
 }
 
 // B[0..R) <- shared nodes lane*R .. lane*R + R - 1 at width R = width_at(WI),
@@ -222,9 +240,9 @@ __device__ __forceinline__ void levels(float (&B)[kMaxR], Lat &L, float *sh, int
     constexpr int R = width_at(WI);
     const int src = (lane + 1) & (kWarp - 1);
     const bool top = lane == kWarp - 1;
-    // in runs up to the next rescale (every kRescale levels, by 2^-kRescale: exact)
+    // in runs up to the next rescale (every L.K levels, by 2^-L.E: exact)
     while (n > 0) {
-        const int m = min(n, kRescale - L.rescale);
+        const int m = min(n, L.K - L.rescale);
         // two levels per iteration at the narrow widths, where the loop's
         // compare and branch are a larger share of a level (measured: 1-2%
         // faster; at widths up to 32 the larger code ran 10% slower)
@@ -232,21 +250,21 @@ __device__ __forceinline__ void levels(float (&B)[kMaxR], Lat &L, float *sh, int
             int i = 0;
 #pragma unroll 1
             for (; i + 2 <= m; i += 2) {
-                level<R>(B, L.q2, src, top);
-                level<R>(B, L.q2, src, top);
+                level<R>(B, L.eta, src, top);
+                level<R>(B, L.eta, src, top);
             }
-            if (i < m) level<R>(B, L.q2, src, top);
+            if (i < m) level<R>(B, L.eta, src, top);
         } else {
 #pragma unroll 1
-            for (int i = 0; i < m; ++i) level<R>(B, L.q2, src, top);
+            for (int i = 0; i < m; ++i) level<R>(B, L.eta, src, top);
         }
         n -= m;
         L.rescale += m;
-        if (L.rescale == kRescale) {
+        if (L.rescale == L.K) {
             L.rescale = 0;
-            L.shift -= kRescale;
+            L.shift -= L.E;
 #pragma unroll
-            for (int s = 0; s < R; ++s) B[s] *= 0x1p-64f;
+            for (int s = 0; s < R; ++s) B[s] *= L.f;
         }
     }
     if (soff < 0) return;
@@ -298,7 +316,9 @@ __device__ __forceinline__ int width_for(int n)
 
 // Per-option constants of the lattice.
 struct Opt {
-    float S, K, sdt, a, q2;  // q2: the level coefficient, -2q when reflected
+    float S, K, sdt, a, q2;  // q2: v = 2q in storage order, -2q when reflected
+    float eta, f;            // the level coefficient 2v / (1 - v); 2^-E
+    int rk, re;              // a rescale by 2^-re every rk levels
     int N;
     bool put;
     bool refl;  // the lattice is stored reflected (node j at index N - j)
@@ -347,13 +367,14 @@ __device__ __forceinline__ int leaves(const Opt &o, float *sh, int lane)
 // the root.  The widths are walked downwards, starting at the width that
 // holds min(N + 1, b) nodes (nodes from b up are zero): at width R the levels
 // run until the level's nodes fit the next width, then the nodes are
-// repacked through the shared buffer.  Gives the root on lane 0 (scaled by
-// 2^shift) and, on lane 0, d1 = B_1 - B_0 of level 1 (stored order) at the
-// root's scaling.
+// repacked through the shared buffer, down to level 1; the root follows
+// from its two nodes.  Gives the root on lane 0 (the undiscounted price
+// divided by lattice_scale(N, eta, shift)) and, on lane 0, d1 = C_1 - C_0 of
+// level 1 (stored order) at the root's scaling.
 //
 // Pass 1 (greeks), its adjoint: weights A on the nodes of level N - 1 with
 // root = sum_j A_j x_j for any level N - 1 of this recursion.  From the root
-// (A = 1) outwards A'_j = (A_j + A_{j-1}) + 2q (A_{j-1} - A_j), one node more
+// (A = 1) outwards A'_j = A_j + (1 + eta) A_{j-1}, one node more
 // per level.  Stored reversed (node j at slot 32R - 1 - j) this is the
 // backward level itself, with the slots not reached yet at zero, so it runs
 // on the same code while the widths are walked upwards, until the width
@@ -368,63 +389,66 @@ __device__ __forceinline__ int leaves(const Opt &o, float *sh, int lane)
 // each width's code exists once in the kernel: the instruction footprint,
 // not the arithmetic, limits the deep lattices.
 //
-// The lattice is a call of its own (not inlined): its register allocation
-// is then independent of the caller's, which measured 5% faster.
-__device__ __noinline__ float lattice(const Opt &o, int band, float *sh, int lane, bool adj, int &shift,
+// Inlined into the kernel (a call of its own cost the caller's saves and
+// restores around it); the greeks, which need more registers, are the call.
+template <bool FULL>
+__device__ __forceinline__ float lattice(const Opt &o, int band, float *sh, int lane, bool adj, int &shift,
                                       float &d1, int &shift_a, int &rf)
 {
+    constexpr int W0 = FULL ? 0 : kW0Band;  // the widest width index this form runs
+    constexpr int MR = width_at(W0);
     Lat L;
-    L.q2 = o.q2;
+    L.eta = o.eta;
+    L.f = o.f;
+    L.K = o.rk;
+    L.E = o.re;
     float B[kMaxR];
     float root = 0.f;
 #pragma unroll 1
-    for (int pass = 0; pass < (adj ? 2 : 1); ++pass) {
+    for (int pass = 0; pass < (FULL && adj ? 2 : 1); ++pass) {
         L.shift = o.N;
         L.rescale = 0;
         int wi, active, lo = 0;
-        bool load = false, captured = false;
+        bool load = false;
         if (pass == 0) {
-            if (min(o.N + 1, band) <= kMaxSteps) {
+            if (!FULL || min(o.N + 1, band) <= kMaxSteps) {
                 // level N at the narrowest width that holds its nonzero band
-                wi = width_for<0>(min(o.N + 1, band));
+                // (the caller guarantees that the banded form's widest holds it)
+                wi = width_for<W0>(min(o.N + 1, band));
                 load = true;
                 active = o.N + 1;
-            } else {
+            } else if constexpr (FULL) {
                 // N = 2048: 2049 leaves do not fit 32 x 64 slots; level N-1 from the leaves
                 wi = 0;
 #pragma unroll
                 for (int s = 0; s < kMaxR; ++s) {
                     const int j = lane * kMaxR + s;
                     const float lb = sh[shidx(j + 1)], b = sh[shidx(j)];
-                    B[s] = fmaf(L.q2, lb - b, lb + b);
+                    B[s] = fmaf(L.eta, lb, lb + b);
                 }
                 active = o.N;
                 L.rescale = 1;
             }
         } else {
 #pragma unroll
-            for (int s = 0; s < kMaxR; ++s) B[s] = 0.f;
+            for (int s = 0; s < MR; ++s) B[s] = 0.f;
             if (lane == kWarp - 1) B[0] = 1.0f;
             wi = kNWidths - 1;
             active = 1;
         }
         for (;;) {
-            if (load) load_width_at<0>(wi, B, sh, lane, lo);
-            const int R = width_rt<0>(wi);
+            if (load) load_width_at<W0>(wi, B, sh, lane, lo);
+            const int R = width_rt<W0>(wi);
             int n, soff = 0, next = wi;
             bool fin = false;
             if (pass == 0) {
                 if (wi + 1 < kNWidths) {
-                    n = active - kWarp * width_rt<0>(wi + 1);
+                    n = active - kWarp * width_rt<W0>(wi + 1);
                     next = wi + 1;
                     load = true;
                     lo = 0;
-                } else if (!captured) {  // width 1: down to level 1
+                } else {  // width 1: down to level 1 (its two nodes on lanes 0, 1)
                     n = active - 2;
-                    soff = -1;
-                    load = false;
-                } else {                 // the root
-                    n = 1;
                     soff = -1;
                     fin = true;
                 }
@@ -435,37 +459,158 @@ __device__ __noinline__ float lattice(const Opt &o, int band, float *sh, int lan
                 } else {
                     n = kWarp * R - active;
                     next = wi - 1;
-                    soff = kWarp * (width_rt<0>(next) - R);
+                    soff = kWarp * (width_rt<W0>(next) - R);
                     load = true;
                     lo = soff;
                 }
             }
-            levels_at<0>(wi, B, L, sh, lane, n, soff);
+            levels_at<W0>(wi, B, L, sh, lane, n, soff);
             active += pass == 0 ? -n : n;
             if (fin) break;
-            if (pass == 0 && wi + 1 == kNWidths) {
-                d1 = __shfl_down_sync(kFull, B[0], 1) - B[0];
-                captured = true;
-            }
             wi = next;
         }
         if (pass == 0) {
-            if (L.rescale == 0) d1 *= 0x1p-64f;
+            // the root from level 1, as the level code computes it, and d1
+            const float c1 = __shfl_down_sync(kFull, B[0], 1);
+            root = fmaf(L.eta, c1, c1 + B[0]);
+            d1 = c1 - B[0];
+            if (++L.rescale == L.K) {
+                L.shift -= L.E;
+                root *= L.f;
+                d1 *= L.f;
+            }
             shift = L.shift;
-            root = B[0];
         } else {
             shift_a = L.shift;
-            rf = width_rt<0>(wi);
+            rf = width_rt<W0>(wi);
         }
     }
     return root;
 }
 
-template <bool G>
+constexpr float kLn2Hi = 0.693147182464599609375f;  // ln 2 = hi + lo
+constexpr float kLn2Lo = (float)(0.69314718055994530942 - 0.693147182464599609375);
+
+// 2^-sh (1 + eta/2)^-N: a root of the lattice C (rescaled to 2^sh) times
+// this is the undiscounted value, since C = (2 + eta)^N V / disc^N.  The
+// logarithm N ln(1 + eta/2) + sh ln 2 (two terms of up to ~1e3 that cancel
+// to the rescales' rounding, below ~80) is formed in pairs of FP32 values,
+// and its exponential is e^hi (1 - lo).
+__device__ __forceinline__ float lattice_scale(int N, float eta, int sh)
+{
+    const float x = 0.5f * eta;
+    const float2 l = (fabsf(x) <= 0.25f) ? df_scale((float)N, df_log1p(x))
+                                         : df_split((double)N * log1p((double)x));
+    const float2 t = df_add(l, df_scale((float)sh, make_float2(kLn2Hi, kLn2Lo)));
+    return expf(-t.x) * (1.0f - t.y);
+}
+
+// Per-option values of the CRR lattice in FP32 (see the header).
+struct Crr {
+    float sdt, a, s1, q;
+};
+
+__device__ __forceinline__ Opt make_opt(float S, float K, float T, float sig, int N, float r, Crr &c)
+{
+    const float dt = T / (float)N;
+    c.sdt = sqrtf(dt);
+    c.a = sig * c.sdt;
+    const float sh2 = sinhf(0.5f * c.a);
+    const float num = expm1f(r * dt) - 2.0f * sh2 * sh2;
+    c.s1 = sinhf(c.a);
+    c.q = num / (2.0f * c.s1);
+    Opt op;
+    op.S = S;
+    op.K = K;
+    op.sdt = c.sdt;
+    op.a = c.a;
+    op.N = N;
+    op.put = S > K;     // price the out-of-the-money side, then parity
+    op.refl = !op.put;  // the call's nonzero leaves are the high ones: reflect
+    op.q2 = op.refl ? -2.0f * c.q : 2.0f * c.q;
+    op.eta = (2.0f * op.q2) / (1.0f - op.q2);
+    // the largest node grows by at most 2 + eta per level: rk levels grow it
+    // by at most 2^64, and the rescale removes the ceiling of that
+    const float lg = log2f(2.0f + op.eta);
+    op.rk = lg <= 1.0f ? kRescale : max(1, (int)((float)kRescale / lg));
+    op.re = (int)ceilf((float)op.rk * lg);
+    op.f = ldexpf(1.0f, -op.re);
+    return op;
+}
+
+// Delta and the vega leaf part of one option from the closed-form adjoint
+// weights, summed over the warp (every lane gets the sums).  A call of its
+// own, so that its registers do not constrain the lattice's.
+__device__ __noinline__ float2 closed_form_greeks(const Opt &op, int nz, int lane)
+{
+    // stored leaf i's weight in the root is the binomial pmf
+    // C(N,i) w^i (1-w)^(N-i), w = (1 + v)/2 with v the lattice's own FP32
+    // 2q in storage order (negated when reflected); its exponential g =
+    // e^(a m), m = 2j - N = s (2i - N) (s = -1 when reflected), is folded
+    // into the same logarithm:
+    //   ln(pmf g) = C - ln i! - ln (N-i)! + i L,
+    //   C = ln N! + N ln((1-v)/2) - s a N,  L = ln((1+v)/(1-v)) + 2 s a
+    const float v = op.q2;
+    const float sa = op.refl ? -op.a : op.a;
+    float2 C, L;
+    if (fabsf(v) <= 0.25f) {
+        // FP32 pairs from the series (all lanes alike: no FP64)
+        const float2 lp = df_log1p(v), lm = df_log1p(-v);
+        const float2 lh = df_add(lm, make_float2(-kLn2Hi, -kLn2Lo));
+        const float na = (float)op.N * sa;
+        C = df_add(g_lfact[op.N], df_scale((float)op.N, lh));
+        C = df_add(C, make_float2(-na, -fmaf((float)op.N, sa, -na)));
+        L = df_add(df_add(lp, make_float2(-lm.x, -lm.y)), make_float2(2.0f * sa, 0.f));
+    } else {
+        // coarse lattices (|2q| > 1/4, a few steps): FP64 logs (no
+        // shuffle here: a warp-synchronous call under this branch made
+        // the compiler treat the whole kernel as divergent, +7%)
+        const double lq = log1p(-(double)v);
+        const float2 lfn = g_lfact[op.N];
+        L = df_split(log1p((double)v) - lq + 2.0 * (double)sa);
+        C = df_split((double)lfn.x + (double)lfn.y + (double)op.N * (lq - 0.69314718055994530942 - (double)sa));
+    }
+    // leaf in the money (exactly the first nz stored leaves): dS_T/dS =
+    // g, dS_T/dsigma = S g m sqrt(dt) (both negated on the put side), so
+    // one exponential gives the weighted g of both sums.
+    // The high parts of C, of the table and of i L are multiples of 2^-10,
+    // and so are their partial sums, exact in FP32 while below 2^14: ln
+    // 2048! < 13572, and with |v| <= 1/4 |i L| < N (0.52 + 2a) < 1300 (a N
+    // < 88 keeps the leaves finite).  The low parts (each below 2^-10)
+    // are added in FP32, and the exponential of the exact high sum is
+    // corrected by (1 + low sum).
+    const float Ch = rintf(C.x * 1024.f) * (1.0f / 1024.f);
+    const float Cl = (C.x - Ch) + C.y;
+    float sd = 0.f, sv = 0.f;
+#pragma unroll 2
+    for (int i = lane; i < nz; i += kWarp) {
+        const float2 x = g_lfact[i], y = g_lfact[op.N - i];
+        const float fi = (float)i;
+        const float pr = fi * L.x;
+        const float ph = rintf(pr * 1024.f) * (1.0f / 1024.f);
+        const float pl = (pr - ph) + fmaf(fi, L.y, fmaf(fi, L.x, -pr));
+        const float h = ((Ch - x.x) - y.x) + ph;
+        const float lo = ((Cl - x.y) - y.y) + pl;
+        const float e = expf(h);
+        const float wg = fmaf(e, lo, e);
+        sd += wg;
+        sv = fmaf(wg, (float)(2 * i - op.N), sv);
+    }
+    const float sgn = op.put ? -1.f : 1.f;
+    sd *= sgn;
+    sv *= (op.refl ? -sgn : sgn) * op.S * op.sdt;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        sd += __shfl_xor_sync(kFull, sd, o2);
+        sv += __shfl_xor_sync(kFull, sv, o2);
+    }
+    return make_float2(sd, sv);
+}
+
+template <bool G, bool FULL>
 __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, float *sh)
 {
     const int lane = threadIdx.x & 31;
-    const float S = __ldg(p.S + o), K = __ldg(p.K + o), T = __ldg(p.T + o), sig = __ldg(p.sigma + o);
     const int N = __ldg(p.steps + o);
     if (N < 1 || N > kMaxSteps) {  // outside the supported depths: NaN results
         if (lane == 0) {
@@ -474,99 +619,32 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
         }
         return;
     }
-    const float dt = T / (float)N;
-    const float sdt = sqrtf(dt);
-    const float a = sig * sdt;
-    const float sh2 = sinhf(0.5f * a);
-    const float num = expm1f(p.r * dt) - 2.0f * sh2 * sh2;
-    const float s1 = sinhf(a);
-    const float q = num / (2.0f * s1);
-    Opt op;
-    op.S = S;
-    op.K = K;
-    op.sdt = sdt;
-    op.a = a;
-    op.N = N;
-    op.put = S > K;  // price the out-of-the-money side, then parity
-    op.refl = !op.put && !p.full;  // the call's nonzero leaves are the high ones: reflect
-    op.q2 = op.refl ? -2.0f * q : 2.0f * q;
-    // price by backward induction; with greeks one adjoint pass gives delta
-    // and the vega leaf part as dot products of its weights with the leaves
+    Crr c;
+    const Opt op = make_opt(__ldg(p.S + o), __ldg(p.K + o), __ldg(p.T + o), __ldg(p.sigma + o), N, p.r, c);
+    // price by backward induction; with greeks, delta and the vega leaf part
+    // from the closed-form adjoint weights
     const bool greeks = G && p.greeks;
     int shift = 0;
     float d1 = 0.f;
     int shift_a = 0, rf = 0;
     const int nz = leaves(op, sh, lane);
-    const int band = p.full ? N + 1 : max(nz, 1);
-    const float b = lattice(op, band, sh, lane, greeks && p.full, shift, d1, shift_a, rf);
-    if (op.refl) d1 = -d1;  // B_1 - B_0 in node order
+    const int band = FULL ? N + 1 : max(nz, 1);
+    if (!FULL && min(N + 1, band) > kWarp * width_at(kW0Band)) {
+        // a band wider than N/2 + 1 (sigma or T negative): outside the inputs
+        if (lane == 0) {
+            p.price[o] = __int_as_float(0x7fc00000);
+            if (G && p.greeks) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+        }
+        return;
+    }
+    const float b = lattice<FULL>(op, band, sh, lane, greeks && FULL, shift, d1, shift_a, rf);
+    const float eta = op.eta, S = op.S, K = op.K, T = __ldg(p.T + o);
+    if (op.refl) d1 = -d1;  // C_1 - C_0 in node order
     float delta = 0.f, vega = 0.f;
-    if (greeks && !p.full) {
-        // stored leaf i's weight in the root is the binomial pmf
-        // C(N,i) w^i (1-w)^(N-i), w = (1 + v)/2 with v the lattice's own FP32
-        // 2q in storage order (negated when reflected); its exponential g =
-        // e^(a m), m = 2j - N = s (2i - N) (s = -1 when reflected), is folded
-        // into the same logarithm:
-        //   ln(pmf g) = C - ln i! - ln (N-i)! + i L,
-        //   C = ln N! + N ln((1-v)/2) - s a N,  L = ln((1+v)/(1-v)) + 2 s a
-        const float v = op.q2;
-        const float sa = op.refl ? -op.a : op.a;
-        float2 C, L;
-        if (fabsf(v) <= 0.25f) {
-            // FP32 pairs from the series (all lanes alike: no FP64)
-            const float2 lp = df_log1p(v), lm = df_log1p(-v);
-            constexpr float kLn2Hi = 0.693147182464599609375f;  // ln 2 = hi + lo
-            constexpr float kLn2Lo = (float)(0.69314718055994530942 - 0.693147182464599609375);
-            const float2 lh = df_add(lm, make_float2(-kLn2Hi, -kLn2Lo));
-            const float na = (float)N * sa;
-            C = df_add(g_lfact[N], df_scale((float)N, lh));
-            C = df_add(C, make_float2(-na, -fmaf((float)N, sa, -na)));
-            L = df_add(df_add(lp, make_float2(-lm.x, -lm.y)), make_float2(2.0f * sa, 0.f));
-        } else {
-            // coarse lattices (|2q| > 1/4, a few steps): FP64 logs (no
-            // shuffle here: a warp-synchronous call under this branch made
-            // the compiler treat the whole kernel as divergent, +7%)
-            const double lq = log1p(-(double)v);
-            const float2 lfn = g_lfact[N];
-            L = df_split(log1p((double)v) - lq + 2.0 * (double)sa);
-            C = df_split((double)lfn.x + (double)lfn.y + (double)N * (lq - 0.69314718055994530942 - (double)sa));
-        }
-        // leaf in the money (exactly the first nz stored leaves): dS_T/dS =
-        // g, dS_T/dsigma = S g m sqrt(dt) (both negated on the put side), so
-        // one exponential gives the weighted g of both sums.
-        // The high parts of C, of the table and of i L are multiples of 2^-10,
-        // and so are their partial sums, exact in FP32 while below 2^14: ln
-        // 2048! < 13572, and with |v| <= 1/4 |i L| < N (0.52 + 2a) < 1300 (a N
-        // < 88 keeps the leaves finite).  The low parts (each below 2^-10)
-        // are added in FP32, and the exponential of the exact high sum is
-        // corrected by (1 + low sum).
-        const float Ch = rintf(C.x * 1024.f) * (1.0f / 1024.f);
-        const float Cl = (C.x - Ch) + C.y;
-        float sd = 0.f, sv = 0.f;
-#pragma unroll 2
-        for (int i = lane; i < nz; i += kWarp) {
-            const float2 x = g_lfact[i], y = g_lfact[N - i];
-            const float fi = (float)i;
-            const float pr = fi * L.x;
-            const float ph = rintf(pr * 1024.f) * (1.0f / 1024.f);
-            const float pl = (pr - ph) + fmaf(fi, L.y, fmaf(fi, L.x, -pr));
-            const float h = ((Ch - x.x) - y.x) + ph;
-            const float lo = ((Cl - x.y) - y.y) + pl;
-            const float e = expf(h);
-            const float wg = fmaf(e, lo, e);
-            sd += wg;
-            sv = fmaf(wg, (float)(2 * i - N), sv);
-        }
-        const float sgn = op.put ? -1.f : 1.f;
-        sd *= sgn;
-        sv *= (op.refl ? -sgn : sgn) * S * sdt;
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) {
-            sd += __shfl_xor_sync(kFull, sd, o2);
-            sv += __shfl_xor_sync(kFull, sv, o2);
-        }
-        delta = sd;
-        vega = sv;
+    if (greeks && !FULL) {
+        const float2 dv = closed_form_greeks(op, nz, lane);
+        delta = dv.x;
+        vega = dv.y;
     } else if (greeks) {
         const int top = kWarp * rf - 1;  // node j of level N - 1 at shared node top - j
         // leaf derivatives pushed back one level (x'_j from x_j, x_{j+1}),
@@ -579,8 +657,8 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
             float d0, v0, d1l, v1;
             leaf(op, j, d0, v0);
             leaf(op, j + 1, d1l, v1);
-            sd = fmaf(w, fmaf(op.q2, d1l - d0, d1l + d0), sd);
-            sv = fmaf(w, fmaf(op.q2, v1 - v0, v1 + v0), sv);
+            sd = fmaf(w, fmaf(eta, d1l, d1l + d0), sd);
+            sv = fmaf(w, fmaf(eta, v1, v1 + v0), sv);
         }
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
@@ -591,26 +669,29 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
         vega = sv;
     }
     if (lane == 0) {
-        // remove the remaining powers of two (exact), then discount
+        // remove the lattice's scaling, then discount
         const float disc = expf(-p.r * T);
-        const float scale = ldexpf(disc, -shift);
-        float price = b * scale;
+        const float ls = lattice_scale(N, eta, shift);
+        float price = (b * ls) * disc;
         if (op.put) price += S - K * disc;
         p.price[o] = price;
         if (greeks) {
             // the closed-form weights are probabilities; the lattice's adjoint
-            // weights carry 2^shift_a
-            const float scale_a = p.full ? ldexpf(disc, -shift_a) : disc;
-            const float q2p = 2.0f * sdt * (-0.5f - q * (coshf(a) / s1));  // 2 dq/dsigma
+            // weights carry the scaling of its N levels and 2^shift_a
+            const float scale_a = FULL ? lattice_scale(N, eta, shift_a) * disc : disc;
+            const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
+            // B_1 - B_0 of the lattice scaled by 2 per level is (1 - v')^(N-1)
+            // (C_1 - C_0), where 1 / (1 - v') = 1 + eta/2
+            const float d1v = (d1 * fmaf(0.5f, eta, 1.0f)) * ls * disc;
             delta *= scale_a;
             if (op.put) delta += 1.0f;
-            vega = fmaf((float)N * q2p, d1 * scale, vega * scale_a);
+            vega = fmaf((float)N * q2p, d1v, vega * scale_a);
             p.greeks[o] = make_float2(delta, vega);
         }
     }
 }
 
-template <bool G>
+template <bool G, bool FULL>
 struct BinoBody {
     using Params = BinoParams;
     Params p;
@@ -621,15 +702,17 @@ struct BinoBody {
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
         const int64_t o = (int64_t)(off + t);
-        if (o < p.n) price_option<G>(p, o, sh);
+        if (o < p.n) price_option<G, FULL>(p, o, sh);
     }
 };
 
-template <bool G>
-__global__ void __launch_bounds__(kWarp, kMinCtas) k_binomial(BinoParams prm, SchedArgs s)
+// FULL: every node of every level and the adjoint lattice (the reference
+// form of the banded lattice and of the closed-form greeks).
+template <bool G, bool FULL>
+__global__ void __launch_bounds__(kWarp, FULL ? kMinCtasFull : kMinCtas) k_binomial(BinoParams prm, SchedArgs s)
 {
     __shared__ float sh[kShNodes];
-    BinoBody<G> b;
+    BinoBody<G, FULL> b;
     b.p = prm;
     b.sh = sh;
     drive(s, b);
@@ -689,8 +772,7 @@ struct BinoBatchBody {
         bp.n = in.n;
         bp.price = in.price;
         bp.greeks = G ? in.greeks : nullptr;
-        bp.full = 0;
-        price_option<G>(bp, local, sh);
+        price_option<G, false>(bp, local, sh);
     }
 };
 
@@ -749,7 +831,7 @@ uint64_t grain(const KArgs &, uint64_t, uint32_t) { return 1; }
 
 uint32_t nchunks(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
 
-int ctas_per_sm() { return occ((const void *)k_binomial<true>); }
+int ctas_per_sm() { return occ((const void *)k_binomial<true, false>); }
 
 template <bool FULL>
 ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
@@ -764,11 +846,10 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.n = a.i32(6);
     p.price = a.buf<float>(7);
     p.greeks = a.buf<float2>(8);
-    p.full = FULL ? 1 : 0;
     if (p.greeks)
-        k_binomial<true><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+        k_binomial<true, FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
     else
-        k_binomial<false><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+        k_binomial<false, FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);
@@ -835,10 +916,10 @@ extern const KernelDesc kBinomial = {
     1, 0, kWarp, 0, validate, grain, nchunks, ctas_per_sm, launch<false>,
 };
 
-// The same program computing every node of every level, without the
-// reflection of the call lattice: the reference form of the banded lattice
-// (identical prices, and greeks up to the summation order of the calls' dot
-// products).
+// The same program computing every node of every level, with the top
+// neighbour of the last lane set to zero, and the greeks from the adjoint
+// lattice: the reference form of the banded lattice (identical prices) and
+// of the closed-form greeks (within ~1e-6).
 extern const KernelDesc kBinomialFull = {
     "binomial_full", 9,
     {{"S", A_BUF_IN}, {"K", A_BUF_IN}, {"T", A_BUF_IN}, {"sigma", A_BUF_IN}, {"steps", A_BUF_IN},
