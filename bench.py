@@ -851,7 +851,7 @@ def run_ours(args):
         for i, (_, name, _, _) in enumerate(progs):
             per[name].append(ev[i].elapsed_time(ev[i + 1]))
     step_ms = max_over_ranks(sum(tot) / len(tot), world)
-    launches = sum(2 if name in ("gemm_split3", "gemm_split6") else 1 for _, name, _, _ in progs)  # split + main
+    launches = sum(2 if name in ("gemm_split3", "gemm_split6", "binomial") else 1 for _, name, _, _ in progs)  # split + main; lattice + greeks
 
     def quantiles(ts):
         q = sorted(ts)

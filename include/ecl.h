@@ -414,7 +414,10 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   backward induction in FP32 by one warp per option (two FP32
  *   instructions per node); with greeks the exact derivatives of the
  *   lattice price with respect to S and sigma, from the lattice's adjoint
- *   weights in closed form (binomial probabilities).  Nodes that are
+ *   weights in closed form (binomial probabilities), in a second, plain
+ *   launch on the engine's stream that reads what the lattice kernel left
+ *   in the greeks buffer (so greeks hold their final values only once the
+ *   run is complete).  Nodes that are
  *   exactly zero (below the strike on the out-of-the-money side) are not
  *   computed.  Inputs: S, K > 0 and T, sigma >= 0; an option whose
  *   out-of-the-money leaves are more than N/2 + 1 (only with sigma or T

@@ -607,23 +607,31 @@ __device__ __noinline__ float2 closed_form_greeks(const Opt &op, int nz, int lan
     return make_float2(sd, sv);
 }
 
-template <bool G, bool FULL>
+// The greeks of the banded form in two launches: the lattice kernel leaves
+// in greeks[o] the scratch pair (nz as int bits, the vega term through p),
+// and the greeks kernel turns it into (delta, vega).  nz = -1 marks an
+// option whose results are NaN.
+__device__ __forceinline__ float2 greeks_scratch(int nz, float d1v) { return make_float2(__int_as_float(nz), d1v); }
+
+// One option by one warp.  FULL: every node, and with greeks the adjoint
+// lattice.  Otherwise the banded lattice and the price; with greeks the
+// scratch pair for k_binomial_greeks.
+template <bool FULL>
 __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, float *sh)
 {
+    const float kNaN = __int_as_float(0x7fc00000);
     const int lane = threadIdx.x & 31;
     const int N = __ldg(p.steps + o);
     if (N < 1 || N > kMaxSteps) {  // outside the supported depths: NaN results
         if (lane == 0) {
-            p.price[o] = __int_as_float(0x7fc00000);
-            if (G && p.greeks) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+            p.price[o] = kNaN;
+            if (p.greeks) p.greeks[o] = FULL ? make_float2(kNaN, kNaN) : greeks_scratch(-1, kNaN);
         }
         return;
     }
     Crr c;
     const Opt op = make_opt(__ldg(p.S + o), __ldg(p.K + o), __ldg(p.T + o), __ldg(p.sigma + o), N, p.r, c);
-    // price by backward induction; with greeks, delta and the vega leaf part
-    // from the closed-form adjoint weights
-    const bool greeks = G && p.greeks;
+    const bool greeks = p.greeks != nullptr;
     int shift = 0;
     float d1 = 0.f;
     int shift_a = 0, rf = 0;
@@ -632,8 +640,8 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     if (!FULL && min(N + 1, band) > kWarp * width_at(kW0Band)) {
         // a band wider than N/2 + 1 (sigma or T negative): outside the inputs
         if (lane == 0) {
-            p.price[o] = __int_as_float(0x7fc00000);
-            if (G && p.greeks) p.greeks[o] = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+            p.price[o] = kNaN;
+            if (greeks) p.greeks[o] = greeks_scratch(-1, kNaN);
         }
         return;
     }
@@ -641,11 +649,7 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     const float eta = op.eta, S = op.S, K = op.K, T = __ldg(p.T + o);
     if (op.refl) d1 = -d1;  // C_1 - C_0 in node order
     float delta = 0.f, vega = 0.f;
-    if (greeks && !FULL) {
-        const float2 dv = closed_form_greeks(op, nz, lane);
-        delta = dv.x;
-        vega = dv.y;
-    } else if (greeks) {
+    if (FULL && greeks) {
         const int top = kWarp * rf - 1;  // node j of level N - 1 at shared node top - j
         // leaf derivatives pushed back one level (x'_j from x_j, x_{j+1}),
         // dotted with A; the leaves are evaluated again here rather than kept
@@ -676,22 +680,56 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
         if (op.put) price += S - K * disc;
         p.price[o] = price;
         if (greeks) {
-            // the closed-form weights are probabilities; the lattice's adjoint
-            // weights carry the scaling of its N levels and 2^shift_a
-            const float scale_a = FULL ? lattice_scale(N, eta, shift_a) * disc : disc;
-            const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
             // B_1 - B_0 of the lattice scaled by 2 per level is (1 - v')^(N-1)
             // (C_1 - C_0), where 1 / (1 - v') = 1 + eta/2
             const float d1v = (d1 * fmaf(0.5f, eta, 1.0f)) * ls * disc;
-            delta *= scale_a;
-            if (op.put) delta += 1.0f;
-            vega = fmaf((float)N * q2p, d1v, vega * scale_a);
-            p.greeks[o] = make_float2(delta, vega);
+            if (FULL) {
+                // the adjoint weights carry the scaling of the N levels and 2^shift_a
+                const float scale_a = lattice_scale(N, eta, shift_a) * disc;
+                const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
+                delta *= scale_a;
+                if (op.put) delta += 1.0f;
+                vega = fmaf((float)N * q2p, d1v, vega * scale_a);
+                p.greeks[o] = make_float2(delta, vega);
+            } else {
+                p.greeks[o] = greeks_scratch(nz, d1v);
+            }
         }
     }
 }
 
-template <bool G, bool FULL>
+// Delta and vega of one option of the banded form from the scratch pair
+// its lattice left in greeks[o] (one warp): the closed-form sums over the
+// nz nonzero leaves (binomial probabilities, discounted), plus 1 for the
+// calls priced through the put, and the vega term through p.
+__device__ __forceinline__ void greeks_option(const BinoParams &p, int64_t o)
+{
+    const float kNaN = __int_as_float(0x7fc00000);
+    const int lane = threadIdx.x & 31;
+    const int N = __ldg(p.steps + o);
+    const float2 sc = p.greeks[o];
+    const int nz = __float_as_int(sc.x);
+    __syncwarp();  // every lane has read the scratch before lane 0 overwrites it
+    // nz outside 0..N+1: a marked option, or a scratch pair that no lattice
+    // wrote (a run that ended with an error): NaN, and nothing indexed by it
+    if (N < 1 || N > kMaxSteps || nz < 0 || nz > N + 1) {
+        if (lane == 0) p.greeks[o] = make_float2(kNaN, kNaN);
+        return;
+    }
+    const float T = __ldg(p.T + o);
+    Crr c;
+    const Opt op = make_opt(__ldg(p.S + o), __ldg(p.K + o), T, __ldg(p.sigma + o), N, p.r, c);
+    const float2 dv = closed_form_greeks(op, nz, lane);
+    if (lane == 0) {
+        const float disc = expf(-p.r * T);
+        const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
+        float delta = dv.x * disc;
+        if (op.put) delta += 1.0f;
+        p.greeks[o] = make_float2(delta, fmaf((float)N * q2p, sc.y, dv.y * disc));
+    }
+}
+
+template <bool FULL>
 struct BinoBody {
     using Params = BinoParams;
     Params p;
@@ -702,20 +740,30 @@ struct BinoBody {
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
         const int64_t o = (int64_t)(off + t);
-        if (o < p.n) price_option<G, FULL>(p, o, sh);
+        if (o < p.n) price_option<FULL>(p, o, sh);
     }
 };
 
 // FULL: every node of every level and the adjoint lattice (the reference
 // form of the banded lattice and of the closed-form greeks).
-template <bool G, bool FULL>
+template <bool FULL>
 __global__ void __launch_bounds__(kWarp, FULL ? kMinCtasFull : kMinCtas) k_binomial(BinoParams prm, SchedArgs s)
 {
     __shared__ float sh[kShNodes];
-    BinoBody<G, FULL> b;
+    BinoBody<FULL> b;
     b.p = prm;
     b.sh = sh;
     drive(s, b);
+}
+
+// The banded form's greeks pass: a plain launch after the lattice kernel on
+// the same stream, one warp per option (8 per CTA).
+constexpr int kGreeksWarps = 8;
+
+__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoParams p)
+{
+    const int64_t o = (int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp;
+    if (o < p.n) greeks_option(p, o);
 }
 
 // ---------------------------------------------------------------- batches
@@ -738,10 +786,36 @@ static_assert(sizeof(BinoInstance) == 80, "ecl_binomial_instance layout");
 struct BinoBatchParams {
     const BinoInstance *inst;
     int32_t count;
+    int32_t greeks;  // with_greeks
     int64_t total;
 };
 
-template <bool G>
+// Instance of global option o (binary search over `first`) as the
+// parameters of one plain batch; false outside every instance.
+__device__ __forceinline__ bool batch_option(const BinoBatchParams &p, int64_t o, BinoParams &bp, int64_t &local)
+{
+    if (o >= p.total) return false;
+    int lo = 0, hi = p.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&p.inst[mid].first) <= o) lo = mid;
+        else hi = mid - 1;
+    }
+    const BinoInstance &in = p.inst[lo];
+    local = o - in.first;
+    if (local < 0 || local >= in.n) return false;
+    bp.S = in.S;
+    bp.K = in.K;
+    bp.T = in.T;
+    bp.sigma = in.sigma;
+    bp.steps = in.steps;
+    bp.r = in.r;
+    bp.n = in.n;
+    bp.price = in.price;
+    bp.greeks = p.greeks ? in.greeks : nullptr;
+    return true;
+}
+
 struct BinoBatchBody {
     using Params = BinoBatchParams;
     Params p;
@@ -751,39 +825,28 @@ struct BinoBatchBody {
 
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
-        const int64_t o = (int64_t)(off + t);
-        if (o >= p.total) return;
-        int lo = 0, hi = p.count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&p.inst[mid].first) <= o) lo = mid;
-            else hi = mid - 1;
-        }
-        const BinoInstance &in = p.inst[lo];
-        const int64_t local = o - in.first;
-        if (local < 0 || local >= in.n) return;
         BinoParams bp;
-        bp.S = in.S;
-        bp.K = in.K;
-        bp.T = in.T;
-        bp.sigma = in.sigma;
-        bp.steps = in.steps;
-        bp.r = in.r;
-        bp.n = in.n;
-        bp.price = in.price;
-        bp.greeks = G ? in.greeks : nullptr;
-        price_option<G, false>(bp, local, sh);
+        int64_t local;
+        if (batch_option(p, (int64_t)(off + t), bp, local)) price_option<false>(bp, local, sh);
     }
 };
 
-template <bool G>
 __global__ void __launch_bounds__(kWarp, kMinCtas) k_binomial_batch(BinoBatchParams prm, SchedArgs s)
 {
     __shared__ float sh[kShNodes];
-    BinoBatchBody<G> b;
+    BinoBatchBody b;
     b.p = prm;
     b.sh = sh;
     drive(s, b);
+}
+
+// The batch's greeks pass (instances with a greeks array), as for one batch.
+__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_batch_greeks(BinoBatchParams prm)
+{
+    BinoParams bp;
+    int64_t local;
+    if (batch_option(prm, (int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp, bp, local) && bp.greeks)
+        greeks_option(bp, local);
 }
 
 int occ(const void *fn)
@@ -831,7 +894,7 @@ uint64_t grain(const KArgs &, uint64_t, uint32_t) { return 1; }
 
 uint32_t nchunks(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
 
-int ctas_per_sm() { return occ((const void *)k_binomial<true, false>); }
+int ctas_per_sm() { return occ((const void *)k_binomial<false>); }
 
 template <bool FULL>
 ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
@@ -846,10 +909,9 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.n = a.i32(6);
     p.price = a.buf<float>(7);
     p.greeks = a.buf<float2>(8);
-    if (p.greeks)
-        k_binomial<true, FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
-    else
-        k_binomial<false, FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    k_binomial<FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    if (!FULL && p.greeks && p.n > 0)
+        k_binomial_greeks<<<(unsigned)((p.n + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0, c.stream>>>(p);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);
@@ -881,7 +943,7 @@ ecl_status v_batch(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
     return ECL_OK;
 }
 
-int batch_ctas_per_sm() { return occ((const void *)k_binomial_batch<true>); }
+int batch_ctas_per_sm() { return occ((const void *)k_binomial_batch); }
 
 ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::string &err)
 {
@@ -889,10 +951,11 @@ ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::
     p.inst = a.buf<const BinoInstance>(0);
     p.count = a.i32(1);
     p.total = a.i64(2);
-    if (a.i32(3))
-        k_binomial_batch<true><<<c.grid, kWarp, 0, c.stream>>>(p, s);
-    else
-        k_binomial_batch<false><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    p.greeks = a.i32(3) ? 1 : 0;
+    k_binomial_batch<<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    if (p.greeks)
+        k_binomial_batch_greeks<<<(unsigned)((p.total + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0,
+                                  c.stream>>>(p);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);
