@@ -418,8 +418,14 @@ __device__ __forceinline__ void drive(const SchedArgs &s, Body &body)
             busy += te - ts;
             nchunks_done += c.t_end - c.t_begin;
             const uint32_t n = c.t_end - c.t_begin;
-            const bool pkg_finished = finish_chunks(s, c.pkg, n, c.nchunks, te);
-            sc.last = pkg_finished ? 1u : 0u;
+            if (s.coverage) {
+                sc.last = finish_chunks(s, c.pkg, n, c.nchunks, te) ? 1u : 0u;
+            } else {
+                // nobody needs to know which CTA finished the package: t1
+                // becomes the latest chunk end without waiting for an atomic
+                finish_chunks_async(s, c.pkg, te);
+                sc.last = 0u;
+            }
         }
         if (s.coverage) {  // debug: count every work-group of a finished package
             __syncthreads();
