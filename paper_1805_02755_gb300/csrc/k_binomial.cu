@@ -174,8 +174,10 @@ __device__ __forceinline__ float2 df_log1p(float x)
 // 32 R'.  Every width is a fully unrolled level loop plus a repack, so the
 // list trades computed-but-dead slots against code size: measured on the
 // 2^20-option batch (price + greeks), finer lists (33 widths: ~96% live
-// slots) ran up to 2x slower on instruction fetch, and this 14-width list
-// (~88% live) was the fastest of eight candidates.
+// slots) ran up to 2x slower on instruction fetch, and this list (~88%
+// live; the banded lattice uses it from 40 down) was the fastest of eight
+// candidates; with the banded lattice at two instructions per node, adding
+// 6, or 14, 10 and 6, or dropping 28 measured 1.5-2% slower.
 constexpr int kWidths[] = {64, 56, 48, 40, 32, 28, 24, 20, 16, 12, 8, 4, 2, 1};
 constexpr int kNWidths = sizeof(kWidths) / sizeof(kWidths[0]);
 __host__ __device__ constexpr int width_at(int i) { return i < kNWidths ? kWidths[i] : 0; }
@@ -243,21 +245,12 @@ __device__ __forceinline__ void levels(float (&B)[kMaxR], Lat &L, float *sh, int
     // in runs up to the next rescale (every L.K levels, by 2^-L.E: exact)
     while (n > 0) {
         const int m = min(n, L.K - L.rescale);
-        // two levels per iteration at the narrow widths, where the loop's
-        // compare and branch are a larger share of a level (measured: 1-2%
-        // faster; at widths up to 32 the larger code ran 10% slower)
-        if constexpr (R <= 16) {
-            int i = 0;
+        // one level per iteration: with four warps per scheduler at different
+        // widths the level code's size costs more than the loop control
+        // (measured: two levels per iteration at widths up to 16 / 32 / 40:
+        // 45.4 / 57.7 / 60.0 ms against 44.7)
 #pragma unroll 1
-            for (; i + 2 <= m; i += 2) {
-                level<R>(B, L.eta, src, top);
-                level<R>(B, L.eta, src, top);
-            }
-            if (i < m) level<R>(B, L.eta, src, top);
-        } else {
-#pragma unroll 1
-            for (int i = 0; i < m; ++i) level<R>(B, L.eta, src, top);
-        }
+        for (int i = 0; i < m; ++i) level<R>(B, L.eta, src, top);
         n -= m;
         L.rescale += m;
         if (L.rescale == L.K) {

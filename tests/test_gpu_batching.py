@@ -65,6 +65,23 @@ def test_uneven_batches_one_launch(E, oracle_mod):
     bb.close()
 
 
+def test_batches_with_and_without_greeks_arrays_in_one_launch(E, oracle_mod):
+    # The greeks of a batch come from a pass after the lattice kernel, which
+    # reads what the lattice left in each instance's greeks array: instances
+    # without an array get prices only, the others their oracle greeks.
+    import torch
+    from paper_1805_02755_gb300.batching import BinomialBatch
+    sizes = [5, 300, 1, 64, 129]
+    batches = make_batches(torch, sizes, 810)
+    for i in (1, 3):
+        batches[i]["greeks"] = None
+    bb = BinomialBatch(batches, with_greeks=True)
+    bb.run()
+    torch.cuda.synchronize()
+    check_batches(batches, oracle_mod)
+    bb.close()
+
+
 def test_graph_replay_equals_eager(E, oracle_mod):
     import torch
     from paper_1805_02755_gb300.batching import BinomialBatch, capture_graph
