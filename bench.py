@@ -358,7 +358,8 @@ class NBody(Workload):
         # FP32 pipe instructions per pair (flops with FMA = 2 in brackets): force 12 [18]
         # (3 sub, 3 FMA, 3 mul, 3 FMA) + 1 rsqrt; energy 7 [10] over i<j (3 sub, 3 FMA,
         # 1 FMA) + 1 rsqrt, which makes it bound by the 16/clk rsqrt unit; adjoint 13 [19];
-        # finite differences 2 x 8 per j for each sample
+        # finite differences: FP64-bound, 2 FP64 instructions per j for each sample
+        # (the FP32 term difference converted, then added)
         if name == "nbody_acc":
             return dict(bound="alu", inst=12.0 * n * n, flops=18.0 * n * n, unit_name="interactions/s", units=n * n)
         if name == "nbody_energy":
@@ -366,7 +367,7 @@ class NBody(Workload):
             return dict(bound="mufu", inst=pairs, flops=10.0 * pairs, unit_name="pairs/s", units=int(pairs))
         if name == "nbody_adjoint":
             return dict(bound="alu", inst=13.0 * n * n, flops=19.0 * n * n, unit_name="interactions/s", units=n * n)
-        return dict(bound="alu", inst=16.0 * n * self.NFD, flops=18.0 * n * self.NFD, unit_name="samples/s",
+        return dict(bound="fp64", inst=2.0 * n * self.NFD, flops=18.0 * n * self.NFD, unit_name="samples/s",
                     units=self.NFD)
 
     def cpu_sample(self, O, threads, f):
@@ -923,12 +924,13 @@ def run_ours(args):
             d["plain_ms"] = ms_plain
             d["adjoint_over_plain"] = ms / ms_plain
             pe.close()
-        if alg["bound"] in ("alu", "mufu"):
-            # FP32 pipe: 128 lanes per SM; rsqrt unit: 16 per SM; per clock at the max SM clock
-            lanes = 128 if alg["bound"] == "alu" else 16
+        if alg["bound"] in ("alu", "mufu", "fp64"):
+            # FP32 pipe: 128 lanes per SM; rsqrt unit: 16 per SM; FP64: 2 instructions per SM
+            # (the nominal 1.25 TFLOP/s of FMA); per clock at the max SM clock
+            lanes = {"alu": 128, "mufu": 16, "fp64": 2}[alg["bound"]]
             peak = sms * lanes * peaks["sm_max_mhz"] * 1e6 / 1e12
             ach = alg["inst"] / (ms * 1e-3) / 1e12
-            unit = "T FP32-inst/s" if alg["bound"] == "alu" else "T rsqrt/s"
+            unit = {"alu": "T FP32-inst/s", "mufu": "T rsqrt/s", "fp64": "T FP64-inst/s"}[alg["bound"]]
             d["roofline"] = dict(bound=alg["bound"], achieved=ach, peak=peak, unit=unit, frac=ach / peak)
             d["fp32_tflops"] = alg["flops"] / (ms * 1e-3) / 1e12
             if "bytes" in alg:

@@ -403,8 +403,10 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *     4 B body int32[s]  5 B comp int32[s]  6 S int32 s  7 B out double[s]
  *   central difference of E in coordinate comp of body: the perturbed
  *   coordinate is rounded to FP32 and the denominator is the FP32 distance
- *   between the two placements; FP32 terms, FP64 sums.  A sample with a
- *   body outside [0, n) or a component outside 0..2 gives NaN.
+ *   between the two placements; FP32 terms, the FP64 sum of their
+ *   differences (each sample's bodies cut into up to 16 segments, added in
+ *   segment order: the result does not depend on the schedule).  A sample
+ *   with a body outside [0, n) or a component outside 0..2 gives NaN.
  *
  * "binomial"  Listing 1 workload (9 args, out pattern 1:32, lws 32)
  *     0 B S float[n]  1 B K float[n]  2 B T float[n]  3 B sigma float[n]

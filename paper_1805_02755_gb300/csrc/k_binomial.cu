@@ -503,6 +503,9 @@ struct Crr {
     float sdt, a, s1, q;
 };
 
+// LAT: also the lattice's coefficient and rescaling (eta, rk, re, f); the
+// greeks pass needs only the CRR values.
+template <bool LAT = true>
 __device__ __forceinline__ Opt make_opt(float S, float K, float T, float sig, int N, float r, Crr &c)
 {
     const float dt = T / (float)N;
@@ -521,20 +524,24 @@ __device__ __forceinline__ Opt make_opt(float S, float K, float T, float sig, in
     op.put = S > K;     // price the out-of-the-money side, then parity
     op.refl = !op.put;  // the call's nonzero leaves are the high ones: reflect
     op.q2 = op.refl ? -2.0f * c.q : 2.0f * c.q;
-    op.eta = (2.0f * op.q2) / (1.0f - op.q2);
-    // the largest node grows by at most 2 + eta per level: rk levels grow it
-    // by at most 2^64, and the rescale removes the ceiling of that
-    const float lg = log2f(2.0f + op.eta);
-    op.rk = lg <= 1.0f ? kRescale : max(1, (int)((float)kRescale / lg));
-    op.re = (int)ceilf((float)op.rk * lg);
-    op.f = ldexpf(1.0f, -op.re);
+    op.eta = 0.f;
+    op.rk = op.re = 0;
+    op.f = 0.f;
+    if (LAT) {
+        op.eta = (2.0f * op.q2) / (1.0f - op.q2);
+        // the largest node grows by at most 2 + eta per level: rk levels grow
+        // it by at most 2^64, and the rescale removes the ceiling of that
+        const float lg = log2f(2.0f + op.eta);
+        op.rk = lg <= 1.0f ? kRescale : max(1, (int)((float)kRescale / lg));
+        op.re = (int)ceilf((float)op.rk * lg);
+        op.f = ldexpf(1.0f, -op.re);
+    }
     return op;
 }
 
 // Delta and the vega leaf part of one option from the closed-form adjoint
-// weights, summed over the warp (every lane gets the sums).  A call of its
-// own, so that its registers do not constrain the lattice's.
-__device__ __noinline__ float2 closed_form_greeks(const Opt &op, int nz, int lane)
+// weights, summed over the warp (every lane gets the sums).
+__device__ __forceinline__ float2 closed_form_greeks(const Opt &op, int nz, int lane)
 {
     // stored leaf i's weight in the root is the binomial pmf
     // C(N,i) w^i (1-w)^(N-i), w = (1 + v)/2 with v the lattice's own FP32
@@ -711,7 +718,7 @@ __device__ __forceinline__ void greeks_option(const BinoParams &p, int64_t o)
     }
     const float T = __ldg(p.T + o);
     Crr c;
-    const Opt op = make_opt(__ldg(p.S + o), __ldg(p.K + o), T, __ldg(p.sigma + o), N, p.r, c);
+    const Opt op = make_opt<false>(__ldg(p.S + o), __ldg(p.K + o), T, __ldg(p.sigma + o), N, p.r, c);
     const float2 dv = closed_form_greeks(op, nz, lane);
     if (lane == 0) {
         const float disc = expf(-p.r * T);

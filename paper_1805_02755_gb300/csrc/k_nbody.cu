@@ -412,6 +412,19 @@ struct EnergyBody {
 };
 
 // ---------------------------------------------------------------- finite differences
+// j-segments per finite-difference sample: enough chunks (about 4096) that
+// the samples spread over every SM, each segment at least one 256-body span.
+constexpr uint32_t kFDSegMax = 16;
+
+__host__ __device__ inline uint32_t fd_segments(int64_t count, int64_t n)
+{
+    uint64_t s = (4096 + (uint64_t)count - 1) / (uint64_t)(count > 0 ? count : 1);
+    if (s > kFDSegMax) s = kFDSegMax;
+    const int64_t spans = (n + kBlock - 1) / kBlock;
+    if ((int64_t)s > spans) s = (uint64_t)spans;
+    return s < 1 ? 1u : (uint32_t)s;
+}
+
 struct FDParams {
     const float4 *pos;
     int64_t n;
@@ -419,29 +432,36 @@ struct FDParams {
     const int *body, *comp;
     int64_t count;
     double *out;
+    double *part;   // [count][seg] FP64 partial sums (seg > 1)
+    unsigned *cnt;  // [count] segments finished per sample
+    uint32_t seg;
 };
 
 struct FDBody {
     static constexpr uint32_t kThreads = kBlock;
     using Params = FDParams;
     Params p;
-    double *dsh;  // [2 * kBlock / 32]
+    double *dsh;  // [kBlock / 32]
 
-    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len)
+    static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t, uint64_t len)
     {
-        return (uint32_t)len;
+        return (uint32_t)(len * q.seg);
     }
 
-    // chunk = one sample: -m_i * (row(q+) - row(q-)) / (x+ - x-),
-    // row(q) = sum_{j != i} m_j / sqrt(|q - r_j|^2 + eps2)
+    // chunk = segment sg of one sample: -m_i * (row(q+) - row(q-)) / (x+ - x-),
+    // row(q) = sum_{j != i} m_j / sqrt(|q - r_j|^2 + eps2), summed as the FP64
+    // sum of the FP32 term differences m_j phi(q+) - m_j phi(q-) (the two
+    // terms are within a factor 2 of each other, so each difference is exact
+    // in FP32); the segments' sums are added in segment order by the last.
     __device__ __forceinline__ void run(uint64_t off, uint64_t, uint32_t t, uint32_t)
     {
-        const int64_t smp = (int64_t)(off + t);
+        const int64_t smp = (int64_t)(off + t / p.seg);
+        const uint32_t sg = t % p.seg;
         if (smp >= p.count) return;
         const int64_t i = p.body[smp];
         const int c = p.comp[smp];
         if (i < 0 || i >= p.n || c < 0 || c > 2) {  // invalid sample: NaN, no access
-            if (threadIdx.x == 0) p.out[smp] = __longlong_as_double(0x7ff8000000000000ll);
+            if (threadIdx.x == 0 && sg == 0) p.out[smp] = __longlong_as_double(0x7ff8000000000000ll);
             return;
         }
         const float4 pi = __ldg(p.pos + i);
@@ -451,8 +471,9 @@ struct FDBody {
         if (c == 0) { qp.x = xp; qm.x = xm; }
         else if (c == 1) { qp.y = xp; qm.y = xm; }
         else { qp.z = xp; qm.z = xm; }
-        double rp = 0.0, rm = 0.0;
-        for (int64_t j = threadIdx.x; j < p.n; j += kBlock) {
+        const int64_t j0 = p.n * (int64_t)sg / p.seg, j1 = p.n * (int64_t)(sg + 1) / p.seg;
+        double acc = 0.0;
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += kBlock) {
             if (j == i) continue;
             const float4 pj = __ldg(p.pos + j);
             float dx = qp.x - pj.x, dy = qp.y - pj.y, dz = qp.z - pj.z;
@@ -461,24 +482,30 @@ struct FDBody {
             dy = qm.y - pj.y;
             dz = qm.z - pj.z;
             const float fm = pj.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, p.eps2))));
-            rp += (double)fp;
-            rm += (double)fm;
+            acc += (double)(fp - fm);
         }
-        rp = warp_sum_d(rp);
-        rm = warp_sum_d(rm);
+        acc = warp_sum_d(acc);
         body_sync(kBlock);
-        if ((threadIdx.x & 31) == 0) {
-            dsh[threadIdx.x / 32] = rp;
-            dsh[kBlock / 32 + threadIdx.x / 32] = rm;
-        }
+        if ((threadIdx.x & 31) == 0) dsh[threadIdx.x / 32] = acc;
         body_sync(kBlock);
         if (threadIdx.x == 0) {
-            double a = 0.0, z = 0.0;
-            for (int q = 0; q < kBlock / 32; ++q) {
-                a += dsh[q];
-                z += dsh[kBlock / 32 + q];
+            double w = 0.0;
+            for (int q = 0; q < kBlock / 32; ++q) w += dsh[q];
+            const double scale = -(double)pi.w / ((double)xp - (double)xm);
+            if (p.seg == 1) {
+                p.out[smp] = scale * w;
+            } else {
+                double *part = p.part + (size_t)smp * p.seg;
+                part[sg] = w;
+                __threadfence();
+                if (atomicAdd(p.cnt + smp, 1u) + 1 == p.seg) {
+                    __threadfence();
+                    double tot = 0.0;
+                    for (uint32_t q = 0; q < p.seg; ++q) tot += *((volatile double *)part + q);
+                    p.out[smp] = scale * tot;
+                    p.cnt[smp] = 0u;  // ready for the next run
+                }
             }
-            p.out[smp] = -(double)pi.w * (a - z) / ((double)xp - (double)xm);
         }
         body_sync(kBlock);
     }
@@ -518,7 +545,7 @@ __global__ void __launch_bounds__(kBlock + 32) k_nbody_energy(EnergyParams prm, 
 
 __global__ void __launch_bounds__(kBlock + 32) k_nbody_fd(FDParams prm, SchedArgs s)
 {
-    __shared__ double dsh[2 * kBlock / 32];
+    __shared__ double dsh[kBlock / 32];
     FDBody b;
     b.p = prm;
     b.dsh = dsh;
@@ -613,8 +640,6 @@ ecl_status check_bodies(const KArgs &a, int pos_arg, int n_arg, uint64_t gws, ui
 bool out4_ok(const KArgs &a, int i, int64_t n) { return a.bytes[i] >= (uint64_t)n * 16 && (uintptr_t)a.ptr[i] % 16 == 0; }
 
 uint64_t grain1(const KArgs &, uint64_t, uint32_t) { return 1; }
-
-uint32_t nchunks_wg(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
 
 // Force kernels: S chunks per work-group (bodies at argument n_arg).
 template <int n_arg>
@@ -803,8 +828,22 @@ ecl_status l_fd(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::str
     p.comp = a.buf<const int>(5);
     p.count = a.i32(6);
     p.out = a.buf<double>(7);
+    p.seg = fd_segments(p.count, p.n);
+    if (p.seg > 1) {
+        const size_t cnt_bytes = ((size_t)p.count * sizeof(unsigned) + 255) / 256 * 256;
+        char *ws = (char *)workspace_get(c.ws, cnt_bytes + (size_t)p.count * p.seg * sizeof(double), err,
+                                         (const void *)k_nbody_fd, c.stream);
+        if (!ws) return ECL_ERR_CUDA;
+        p.cnt = (unsigned *)ws;
+        p.part = (double *)(ws + cnt_bytes);
+    }
     k_nbody_fd<<<c.grid, kBlock + 32, 0, c.stream>>>(p, s);
     return launched(err);
+}
+
+uint32_t nchunks_fd(const KArgs &a, uint64_t, uint32_t, uint64_t, uint64_t len)
+{
+    return (uint32_t)(len * fd_segments(a.i32(6), a.i32(1)));
 }
 
 int o_fd() { return occ((const void *)k_nbody_fd); }
@@ -841,7 +880,7 @@ extern const KernelDesc kNBodyFD = {
     "nbody_fd", 8,
     {{"in_pos", A_BUF_IN}, {"bodies", A_I32}, {"esp_sqr", A_F32}, {"h", A_F32}, {"body", A_BUF_IN},
      {"comp", A_BUF_IN}, {"count", A_I32}, {"out", A_BUF_OUT}},
-    1, 1, kBlock + 32, 0, v_fd, grain1, nchunks_wg, o_fd, l_fd,
+    1, 1, kBlock + 32, 0, v_fd, grain1, nchunks_fd, o_fd, l_fd,
 };
 
 // ---------------------------------------------------------------- energy without allocation
