@@ -143,10 +143,11 @@ __device__ __forceinline__ void horizontal_store(const GaussParams &p, const Chu
 // 31-tap path.  The chunk's input tile (62 rows x 256 columns: image
 // columns x0-16 .. x0+239, rows clamped to the image) is staged in shared
 // memory with 16-byte cp.async copies (element-wise clamped loads at the
-// left/right borders).  The vertical pass then reads shared memory at
-// compile-time offsets, with the 31 weights and the 32 outputs of a column
-// in registers; its results overwrite the staged rows and feed the
-// horizontal pass.
+// left/right borders), in two groups of rows (0..31, 32..61) so that the
+// vertical pass starts on the first while the second is in flight.  The
+// vertical pass reads shared memory at compile-time offsets, with the 31
+// weights and the 32 outputs of a column in registers; its results
+// overwrite the staged rows and feed the horizontal pass.
 constexpr int kNIN = kRB + 30;   // staged input rows
 constexpr int kSC = kSW / 4;     // 16-byte chunks per staged row
 
@@ -168,20 +169,21 @@ struct Gauss31Body {
         return gauss_nchunks(q, off, len);
     }
 
-    __device__ __forceinline__ void stage(const ChunkGeom &g)
+    // Staged rows [kb, ke) (kb a multiple of 4) as one group of copies.
+    __device__ __forceinline__ void stage(const ChunkGeom &g, int kb, int ke)
     {
         const bool vec_ok = (p.W % 4) == 0 && ((uintptr_t)p.in % 16) == 0;
         const int c4 = threadIdx.x % kSC;  // fixed 16-byte column chunk per thread
         const int64_t xs = g.x0 - 16 + 4 * c4;
         const bool vec = vec_ok && xs >= 0 && xs + 4 <= p.W;
-        const int k0 = threadIdx.x / kSC;
+        const int k0 = kb + threadIdx.x / kSC;
         const int64_t ylo = g.y0 - 15 + k0;
-        if (vec && ylo >= 0 && g.y0 - 15 + kNIN <= p.H) {  // interior rows: pointer steps, no clamps
+        if (vec && g.y0 - 15 + kb >= 0 && g.y0 - 15 + ke <= p.H) {  // interior rows: pointer steps, no clamps
             const float *src = p.in + ylo * p.W + xs;
             const int64_t step = (int64_t)(kBlock / kSC) * p.W;
-            for (int k = k0; k < kNIN; k += kBlock / kSC, src += step) cp_async16(&st[k][4 * c4], src);
+            for (int k = k0; k < ke; k += kBlock / kSC, src += step) cp_async16(&st[k][4 * c4], src);
         } else {
-            for (int k = k0; k < kNIN; k += kBlock / kSC) {
+            for (int k = k0; k < ke; k += kBlock / kSC) {
                 const int64_t ys = clampl(g.y0 - 15 + k, 0, p.H - 1);
                 const float *row = p.in + ys * p.W;
                 float *dst = &st[k][4 * c4];
@@ -193,7 +195,7 @@ struct Gauss31Body {
                 }
             }
         }
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
 
     __device__ __forceinline__ void run(uint64_t off, uint64_t len, uint32_t t, uint32_t) { tile(geom(p, off, len, t)); }
@@ -201,7 +203,12 @@ struct Gauss31Body {
     // One 32-row x 224-column output tile of the image p.
     __device__ __forceinline__ void tile(const ChunkGeom &g)
     {
-        stage(g);
+        // the staged rows in two groups of copies: the vertical pass starts on
+        // the first while the second is in flight
+        constexpr int kHalf = 32;
+        stage(g, 0, kHalf);
+        stage(g, kHalf, kNIN);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         body_sync(kBlock);
         // vertical pass: staged column c <-> image column x0 - 16 + c, one column per thread
         float acc[kRB];
@@ -209,7 +216,16 @@ struct Gauss31Body {
 #pragma unroll
         for (int o = 0; o < kRB; ++o) acc[o] = 0.f;
 #pragma unroll
-        for (int k = 0; k < kNIN; ++k) {
+        for (int k = 0; k < kHalf; ++k) {
+            const float v = st[k][c1];
+#pragma unroll
+            for (int o = 0; o < kRB; ++o)
+                if (k - o >= 0 && k - o < 31) acc[o] = fmaf(wr[k - o], v, acc[o]);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        body_sync(kBlock);
+#pragma unroll
+        for (int k = kHalf; k < kNIN; ++k) {
             const float v = st[k][c1];
 #pragma unroll
             for (int o = 0; o < kRB; ++o)
