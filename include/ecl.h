@@ -176,6 +176,17 @@ ecl_status ecl_engine_set_stream(ecl_engine *e, void *cuda_stream);
  * keeps the synchronous run of Listing 1.  Errors: ECL_ERR_ARG, ECL_ERR_CUDA. */
 ecl_status ecl_engine_copy_streams(ecl_engine *e, void *h2d_stream, void *d2h_stream, int async);
 
+/* Time of a run's main kernel, for the Introspector's per-execution timings
+ * (Sec. 5.2) and the time measurements of Sec. 7.3.  With two CUDA events
+ * set (cudaEvent_t passed as void *, created by the caller with timing,
+ * owned by the caller, NULL and NULL to clear), every later run records
+ * `begin` on the engine's stream right before the program's main kernel and
+ * `end` right after it: a pass before it (the split GEMMs' operand split)
+ * or after it (the binomial's greeks pass) falls outside.  The events are
+ * not synchronised; read them with cudaEventElapsedTime once the run is
+ * complete.  Errors: ECL_ERR_ARG if only one of the two is NULL. */
+ecl_status ecl_engine_kernel_events(ecl_engine *e, void *begin, void *end);
+
 /* Global and local work size (Listing 2 "work_items"; Listing 1 sets them
  * one at a time).  gws must be a positive multiple of lws; each kernel
  * also restricts lws (see the kernel list below).  G = gws / lws. */

@@ -63,6 +63,7 @@ def lib():
             "ecl_engine_destroy": (None, [_vp]),
             "ecl_engine_set_stream": (_st, [_vp, _vp]),
             "ecl_engine_copy_streams": (_st, [_vp, _vp, _vp, ctypes.c_int]),
+            "ecl_engine_kernel_events": (_st, [_vp, _vp, _vp]),
             "ecl_work_items": (_st, [_vp, ctypes.c_uint64, ctypes.c_uint32]),
             "ecl_scheduler": (_st, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
             "ecl_workers": (_st, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -147,6 +148,18 @@ def ecl_engine_copy_streams(e, h2d_stream=None, d2h_stream=None, asynchronous: b
     h2d = 0 if h2d_stream is None else _stream_handle(h2d_stream)  # None: the engine's own stream
     d2h = 0 if d2h_stream is None else _stream_handle(d2h_stream)
     _check(lib().ecl_engine_copy_streams(e, _vp(h2d), _vp(d2h), 1 if asynchronous else 0), e)
+
+
+def _event_handle(ev) -> int:
+    if ev is None:
+        return 0
+    if isinstance(ev, int):
+        return ev
+    return ev.cuda_event  # torch.cuda.Event (created with enable_timing=True)
+
+
+def ecl_engine_kernel_events(e, begin=None, end=None) -> None:
+    _check(lib().ecl_engine_kernel_events(e, _vp(_event_handle(begin)), _vp(_event_handle(end))), e)
 
 
 def ecl_work_items(e, gws: int, lws: int) -> None:
@@ -493,6 +506,13 @@ class Engine:
         launch; with asynchronous=True run() returns at once and
         synchronize() waits for the results (include/ecl.h)."""
         ecl_engine_copy_streams(self.h, h2d, d2h, asynchronous)
+        return self
+
+    def kernel_events(self, begin=None, end=None):
+        """Events recorded right before and after each later run's main
+        kernel (include/ecl.h); None, None clears them."""
+        ecl_engine_kernel_events(self.h, begin, end)
+        self._kernel_events = (begin, end)  # kept alive with the engine
         return self
 
     def run(self):

@@ -122,7 +122,32 @@ struct LaunchCtx {
     uint64_t gws;
     uint32_t grid;
     Workspace *ws;
+    // ecl_engine_kernel_events: a launcher that follows its main kernel with
+    // another (the binomial's greeks pass) records mark_end right after the
+    // main kernel and sets *marked; otherwise the run records it after the
+    // launcher returns
+    cudaEvent_t mark_end = nullptr;
+    bool *marked = nullptr;
+    // the same for the begin mark, recorded before the launcher; a launcher
+    // with a pass before its main kernel (the split GEMMs' operand split)
+    // records it again after that pass (the later record counts)
+    cudaEvent_t mark_begin = nullptr;
 };
+
+// Records c.mark_begin on the launch's stream before a program's main kernel.
+inline void mark_main_begin(const LaunchCtx &c)
+{
+    if (c.mark_begin) cudaEventRecord(c.mark_begin, c.stream);
+}
+
+// Records c.mark_end on the launch's stream after a program's main kernel.
+inline void mark_main_end(const LaunchCtx &c)
+{
+    if (c.mark_end && c.marked) {
+        cudaEventRecord(c.mark_end, c.stream);
+        *c.marked = true;
+    }
+}
 
 struct KernelDesc {
     const char *name;

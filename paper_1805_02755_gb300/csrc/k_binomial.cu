@@ -910,6 +910,7 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.price = a.buf<float>(7);
     p.greeks = a.buf<float2>(8);
     k_binomial<FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    mark_main_end(c);
     if (!FULL && p.greeks && p.n > 0)
         k_binomial_greeks<<<(unsigned)((p.n + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0, c.stream>>>(p);
     cudaError_t ce = cudaGetLastError();
@@ -953,6 +954,7 @@ ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::
     p.total = a.i64(2);
     p.greeks = a.i32(3) ? 1 : 0;
     k_binomial_batch<<<c.grid, kWarp, 0, c.stream>>>(p, s);
+    mark_main_end(c);
     if (p.greeks)
         k_binomial_batch_greeks<<<(unsigned)((p.total + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0,
                                   c.stream>>>(p);

@@ -490,6 +490,7 @@ ecl_status l_split(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::
         err = std::string("split launch: ") + cudaGetErrorString(ce);
         return ECL_ERR_CUDA;
     }
+    mark_main_begin(c);
     Maps maps;
     if (!make_map(&maps.a[0], ah, M, K, BM, err) || !make_map(&maps.a[1], alo, M, K, BM, err) ||
         !make_map(&maps.b[0], bh, N, K, BN, err) || !make_map(&maps.b[1], blo, N, K, BN, err))

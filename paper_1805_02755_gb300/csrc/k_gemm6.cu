@@ -469,6 +469,7 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
         err = std::string("split launch: ") + cudaGetErrorString(ce);
         return ECL_ERR_CUDA;
     }
+    mark_main_begin(c);
     Maps6 maps;
     for (int q = 0; q < 3; ++q)
         if (!make_map(&maps.a[q], a3 + q * na, M, K, BM, err) || !make_map(&maps.b[q], b3 + q * nb, N, K, BN, err))

@@ -149,6 +149,8 @@ struct ecl_engine {
     bool copies_set = false, host_async = false;
     cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_out = nullptr;
     bool ev_pending = false;  // ev_done / ev_out record a run not yet waited for
+    // caller's events around each run's main kernel (ecl_engine_kernel_events)
+    cudaEvent_t kev_begin = nullptr, kev_end = nullptr;
     // facts of the last run
     uint64_t last_G = 0, last_npkg = 0;
     uint32_t last_D = 0, last_C = 0, last_grid = 0, last_mode = MODE_MONO;
@@ -437,6 +439,14 @@ ecl_status ecl_engine_copy_streams(ecl_engine *e, void *h2d_stream, void *d2h_st
     e->d2h = (cudaStream_t)d2h_stream;
     e->copies_set = true;
     e->host_async = async != 0;
+    return ECL_OK;
+}
+
+ecl_status ecl_engine_kernel_events(ecl_engine *e, void *begin, void *end)
+{
+    if (!e || (!begin) != (!end)) return ECL_ERR_ARG;
+    e->kev_begin = (cudaEvent_t)begin;
+    e->kev_end = (cudaEvent_t)end;
     return ECL_OK;
 }
 
@@ -879,8 +889,16 @@ ecl_status ecl_run(ecl_engine *e)
     lc.gws = e->gws;
     lc.grid = grid;
     lc.ws = &e->ws;
+    bool marked = false;
+    if (e->kev_begin) {
+        CUDA_OR_FAIL(e, cudaEventRecord(e->kev_begin, e->stream));
+        lc.mark_begin = e->kev_begin;
+        lc.mark_end = e->kev_end;
+        lc.marked = &marked;
+    }
     st = k->launch(a, s, lc, err);
     if (st != ECL_OK) return fail(e, st, "%s: %s", k->name, err.c_str());
+    if (e->kev_end && !marked) CUDA_OR_FAIL(e, cudaEventRecord(e->kev_end, e->stream));
     e->last_G = G;
     e->last_npkg = pl.mode == MODE_HGUIDED ? 0 : pl.table.size();
     e->last_D = D;

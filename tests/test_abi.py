@@ -86,6 +86,7 @@ def test_null_handles(E):
     assert L.ecl_engine_create(None, 0, None) == E.ECL_ERR_ARG
     L.ecl_engine_destroy(None)
     assert L.ecl_last_error(None) == b"NULL engine"
+    assert L.ecl_engine_kernel_events(None, None, None) == E.ECL_ERR_ARG
 
 
 def _table2():

@@ -140,3 +140,43 @@ def test_deep_out_of_the_money_band_of_one_leaf(E, oracle_mod):
     pf, gf, _ = run_bino(E, o, kernel="binomial_full")
     assert np.array_equal(price.view(np.uint32), pf.view(np.uint32))
     check(o, price, gr, oracle_mod)
+
+
+def test_kernel_events_time_the_lattice_kernel_alone(E):
+    # ecl_engine_kernel_events: the events bracket the lattice kernel, not the
+    # greeks pass after it, so they span less than the whole run; the results
+    # are those of a run without events
+    import torch
+    o = W.binomial_options(4096, seed=47)
+    n = len(o["S"])
+    t = {k: torch.from_numpy(np.ascontiguousarray(o[k])).cuda() for k in ("S", "K", "T", "sigma", "steps")}
+    outs = []
+    for with_events in (False, True):
+        price = torch.full((n,), -1.0, device="cuda")
+        gr = torch.full((n, 2), -1.0, device="cuda")
+        eng = E.Engine(0)
+        p = E.Program("binomial")
+        for k in ("S", "K", "T", "sigma", "steps"):
+            p.in_(t[k])
+        p.out(price).out(gr)
+        p.args(t["S"], t["K"], t["T"], t["sigma"], t["steps"], o["r"], n, price, gr)
+        eng.work_items(n * 32, 32).scheduler("hguided", (2.0, 1.0)).workers(8, 0).program(p)
+        stream = torch.cuda.current_stream()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if with_events:
+            k0.record(stream)
+            k1.record(stream)
+            eng.kernel_events(k0, k1)
+        a.record(stream)
+        eng.run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if with_events:
+            whole, main = a.elapsed_time(b), k0.elapsed_time(k1)
+            assert 0 < main < whole, (main, whole)
+            assert a.elapsed_time(k0) >= 0 and k1.elapsed_time(b) > 0
+            eng.kernel_events(None, None)
+        outs.append((price.cpu().numpy(), gr.cpu().numpy()))
+        eng.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
