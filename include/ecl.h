@@ -472,7 +472,8 @@ ecl_status ecl_nbody_energy_noalloc(const void *pos4, int32_t n, float eps2, dou
  *   arrays the table points to.
  *
  * "gemm_bf16"  (6 args; lws 32768 = one 128 x 256 output tile; the
- *   scheduling unit is one row of tiles)
+ *   scheduling unit is two rows of tiles: a CTA computes two vertically
+ *   adjacent tiles together)
  *     0 B A bf16[M*K] row-major  1 B Bt bf16[N*K] row-major (B transposed)
  *     2 B C float[M*N] row-major  3 S int32 M  4 S int32 N  5 S int32 K
  *   C = A B, FP32 accumulation in tensor memory (tcgen05).  gws =

@@ -2,25 +2,32 @@
 //
 //   C[M x N] (FP32, row-major) = A[M x K] (bf16, row-major) * Bt[N x K]^T
 //
-// The NDRange is the grid of 128 x 256 output tiles, numbered in column
-// groups (tc::tile_at: the tiles of W tile columns row by row, then the next
-// W columns), so that a wave of concurrent tiles reads few strips of A and
-// Bt; one work-group = one tile, and the scheduling unit is as many tiles as a
-// tile row holds, so Static / Dynamic / HGuided hand out packages of whole
-// grains of that size.
+// The NDRange is the grid of 128 x 256 output tiles: one work-group = one
+// tile (the config's 128-row tiles).  A chunk is a pair of vertically
+// adjacent tiles, one 256 x 256 block computed together: each staged slice
+// of Bt feeds two MMAs, twice the MMA work per staged byte of a single
+// tile (measured at 8192^3: 0.749 -> 0.649 ms).  Pairs are numbered in
+// column groups (tc::tile_at: the pairs of W tile columns row by row, then
+// the next W columns), so that a wave of concurrent pairs reads few strips
+// of A and Bt; with an odd number of tile rows the last row's tiles follow
+// as single-tile chunks.  The scheduling unit is two tile rows, so Static /
+// Dynamic / HGuided hand out packages of whole pairs of tile rows.
 //
 // Each persistent CTA (192 threads, one per SM) is warp-specialised:
-//   warp 0    claims chunks (tiles) from the package queue and feeds a ring
-//             of tile slots; its lane 0 issues the TMA loads (128B swizzle)
-//             of the 64-wide K slices of A and Bt into a 4-stage ring;
-//   warp 1    allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
-//             and its lane 0 issues tcgen05.mma (M128 N256 K16, BF16 inputs,
-//             FP32 accumulation), committing each stage back to the loader
-//             and each finished accumulator to the epilogue;
-//   warps 2-5 read the accumulator with tcgen05.ld (each warp its 32-lane
+//   warp 0    claims chunks from the package queue and feeds a ring of
+//             chunk slots; its lane 0 issues the TMA loads (128B swizzle)
+//             of the 64-wide K slices of A (256 rows) and Bt (256 rows)
+//             into a 3-stage ring of 64 KB stages;
+//   warp 1    allocates 512 TMEM columns (the pair's two 128 x 256 FP32
+//             accumulators) and its lane 0 issues tcgen05.mma (M128 N256
+//             K16, BF16 inputs, FP32 accumulation), two per K16 step, one
+//             per tile of the pair, committing each stage back to the
+//             loader and the finished pair to the epilogue;
+//   warps 2-5 read both accumulators with tcgen05.ld (each warp its 32-lane
 //             quarter of TMEM), store FP32 to C with 128-bit stores, free the
-//             accumulator and account for the finished chunk.
-// The epilogue of one tile overlaps the main loop of the next.
+//             accumulators and account for the finished chunk.
+// The loads of the next pair's first stages overlap the epilogue; its MMAs
+// wait for the accumulators to be free.
 //
 // Split mode (gemm_split3): A and Bt are FP32; a first kernel splits every
 // value x into hi = bf16(x) and lo = bf16(x - hi) (the subtraction is exact
@@ -44,11 +51,15 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BN = 256, BK = 64, NSTAGE = 4, RING = 4;
-constexpr int STAGE_A = BM * BK * 2;  // 16 KB
+// A work-group is one BM x BN output tile; a chunk is a pair of vertically
+// adjacent tiles (CM = 2 BM rows), computed together so that each staged
+// slice of Bt feeds two MMAs: twice the MMA work per staged byte of a
+// single tile.
+constexpr int BM = 128, BN = 256, BK = 64, PAIR = 2, CM = PAIR * BM, NSTAGE = 3, RING = 4;
+constexpr int STAGE_A = CM * BK * 2;  // 32 KB
 constexpr int STAGE_B = BN * BK * 2;  // 32 KB
 constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_COLS = 512;   // the pair's two 128 x 256 FP32 accumulators
 constexpr int64_t TILE_DONE = -1;
 constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
@@ -56,7 +67,7 @@ struct __align__(1024) GemmSmem {
     uint8_t a[NSTAGE][STAGE_A];
     uint8_t b[NSTAGE][STAGE_B];
     uint64_t full[NSTAGE], empty[NSTAGE];
-    uint64_t tfull[2], tempty[2];
+    uint64_t tfull, tempty;  // the accumulators (one pair at a time)
     uint64_t rfull[RING], rempty[RING];
     uint64_t drain;
     uint64_t stored;  // the four epilogue warps finished storing a tile
@@ -75,15 +86,61 @@ struct GemmParams {
     float *C;
     int64_t M, N, K;
     int64_t tiles_n;
-    tc::TileOrder order;  // work-group id -> output tile
+    int64_t tmf;          // full pairs of tile rows (floor(tile rows / 2))
+    tc::TileOrder order;  // pair id -> pair row, tile column
     uint32_t kblocks;   // K slices per sweep
     uint32_t sweeps;    // 1 (bf16) or 3 (split)
 };
 
+// Work-groups and chunks.  The first F = 2 tmf tn work-groups (tmf full
+// pairs of tile rows, tn tile columns) are the tile pairs, two work-groups
+// each, numbered in column groups (tc::tile_at over the tmf x tn grid of
+// pairs); with an odd number of tile rows the last row's tn tiles follow,
+// one work-group and one chunk each.  Packages hold whole pairs of tile rows
+// (grain 2 tn), so a package starts at an even work-group, and only the
+// last package reaches past F.
+__host__ __device__ inline uint32_t gemm_chunks(int64_t F, uint64_t off, uint64_t len)
+{
+    const uint64_t b = off + len, f = (uint64_t)F;
+    const uint64_t pairs = off < f ? ((b < f ? b : f) - off) / PAIR : 0;
+    const uint64_t singles = b > f ? b - (off > f ? off : f) : 0;
+    return (uint32_t)(pairs + singles);
+}
+
+// Chunk code of chunk t of the package at `off`: a pair id below tmf tn, a
+// single tile of the last row (tmf tn + its column) from there on.
+__host__ __device__ inline int64_t gemm_chunk_code(int64_t F, int64_t tmf_tn, uint64_t off, uint64_t t)
+{
+    const uint64_t f = (uint64_t)F;
+    const uint64_t cp = off < f ? (f - off) / PAIR : 0;  // pairs from off up to F
+    if (t < cp) return (int64_t)(off / PAIR + t);
+    const uint64_t w = (off > f ? off : f) + (t - cp);   // a work-group of the last row
+    return tmf_tn + (int64_t)(w - f);
+}
+
 struct GemmBody {  // chunk bookkeeping for the scheduler
     using Params = GemmParams;
-    static __host__ __device__ uint32_t nchunks(const Params &, uint64_t, uint64_t len) { return (uint32_t)len; }
+    static __host__ __device__ uint32_t nchunks(const Params &q, uint64_t off, uint64_t len)
+    {
+        return gemm_chunks(2 * q.tmf * q.tiles_n, off, len);
+    }
 };
+
+// First row and column of chunk `code` (its 256 rows; the rows from M on are
+// neither loaded, TMA fills them with zeros, nor stored).
+__device__ __forceinline__ void chunk_origin(const GemmParams &p, int64_t code, int &m0, int &n0)
+{
+    const int64_t full = p.tmf * p.tiles_n;
+    if (code < full) {
+        int64_t pr, nt;
+        tc::tile_at(p.order, code, pr, nt);
+        m0 = (int)(pr * CM);
+        n0 = (int)(nt * BN);
+    } else {
+        m0 = (int)(p.tmf * CM);
+        n0 = (int)((code - full) * BN);
+    }
+}
 
 // ---------------------------------------------------------------- kernel
 struct Maps {
@@ -107,10 +164,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm.full[i], 1);
             mbar_init(&sm.empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&sm.tfull[i], 1);
-            mbar_init(&sm.tempty[i], 4);
-        }
+        mbar_init(&sm.tfull, 1);
+        mbar_init(&sm.tempty, 4);
         for (int i = 0; i < RING; ++i) {
             mbar_init(&sm.rfull[i], 1);
             mbar_init(&sm.rempty[i], 5);  // MMA lane + one lane per epilogue warp
@@ -154,18 +209,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (!sm.t_first) sm.t_first = gtime();
                 }
                 for (uint32_t t = c.t_begin; t < c.t_end && !*err; ++t) {
-                    const int64_t tile = (int64_t)(c.off + t);
+                    const int64_t code = gemm_chunk_code(2 * p.tmf * p.tiles_n, p.tmf * p.tiles_n, c.off, t);
                     const uint32_t r = ri % RING;
                     if (!mbar_wait(&sm.rempty[r], ((ri / RING) & 1) ^ 1, err, gerr)) break;
-                    sm.ring_tile[r] = tile;
+                    sm.ring_tile[r] = code;
                     sm.ring_pkg[r] = c.pkg;
                     sm.ring_nch[r] = c.nchunks;
                     mbar_arrive(&sm.rfull[r]);
                     ++ri;
-                    int64_t mt, nt;
-                    tc::tile_at(p.order, tile, mt, nt);
-                    const int m0 = (int)(mt * BM);
-                    const int n0 = (int)(nt * BN);
+                    int m0, n0;
+                    chunk_origin(p, code, m0, n0);
                     for (uint32_t k = 0; k < ksteps; ++k, ++kq) {
                         const uint32_t st = kq % NSTAGE;
                         if (!mbar_wait(&sm.empty[st], ((kq / NSTAGE) & 1) ^ 1, err, gerr)) break;
@@ -207,10 +260,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_arrive(&sm.rempty[r]);
                 ++ri;
                 if (tile == TILE_DONE) break;
-                const uint32_t buf = tc & 1;
-                if (!mbar_wait(&sm.tempty[buf], ((tc >> 1) & 1) ^ 1, err, gerr)) break;
+                // the epilogue of the previous pair has read both accumulators
+                if (!mbar_wait(&sm.tempty, (tc & 1) ^ 1, err, gerr)) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + buf * BN;
                 bool ok = true;
                 for (uint32_t k = 0; k < ksteps; ++k, ++kq) {
                     const uint32_t st = kq % NSTAGE;
@@ -220,14 +272,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sm.a[st]), b0 = smem_u32(sm.b[st]);
+                    // A rows h * 128 .. + 127 of the stage (16 KB apart, 128B swizzle
+                    // atoms of 8 rows) into accumulator h, the Bt slice shared
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)
-                        umma(dt, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC, (k | kk) != 0);
+#pragma unroll
+                        for (int h = 0; h < PAIR; ++h)
+                            umma(tmem + h * BN, sdesc(a0 + h * (BM * BK * 2) + kk * 32), sdesc(b0 + kk * 32), IDESC,
+                                 (k | kk) != 0);
                     umma_commit(&sm.empty[st]);
                     issued = true;
                 }
                 if (!ok) break;
-                umma_commit(&sm.tfull[buf]);
+                umma_commit(&sm.tfull);
                 ++tc;
             }
             if (issued) {  // every MMA issued by this CTA has completed
@@ -262,20 +319,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             nch = __shfl_sync(0xffffffffu, nch, 0);
             ++ri;
             if (tile == TILE_DONE) break;
-            const uint32_t buf = tc & 1;
-            if (lane == 0) ok = mbar_wait(&sm.tfull[buf], (tc >> 1) & 1, err, gerr);
+            if (lane == 0) ok = mbar_wait(&sm.tfull, tc & 1, err, gerr);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
-            int64_t mt, nt;
-            tc::tile_at(p.order, tile, mt, nt);
-            const int64_t m = mt * BM + quarter * 32 + lane;
-            const int64_t n0 = nt * BN;
+            int cm0, cn0;
+            chunk_origin(p, tile, cm0, cn0);
+            const int64_t n0 = cn0;
             const bool vec = (p.N % 4) == 0;
 #pragma unroll 1
-            for (int cc = 0; cc < BN / 32; ++cc) {
+            for (int q = 0; q < PAIR * (BN / 32); ++q) {
+                const int h = q / (BN / 32), cc = q % (BN / 32);  // tile h of the pair, 32 columns cc
+                const int64_t m = (int64_t)cm0 + h * BM + quarter * 32 + lane;
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN + cc * 32, v);
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + h * BN + cc * 32, v);
                 const int64_t c0 = n0 + cc * 32;
                 if (m < p.M) {
                     float *row = p.C + m * p.N;
@@ -293,7 +350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(&sm.tempty[buf]);
+                mbar_arrive(&sm.tempty);
                 mbar_arrive(&sm.stored);
             }
             // chunk accounting once all four warps stored the tile (bounded wait)
@@ -431,7 +488,15 @@ ecl_status v_split(const KArgs &a, uint64_t gws, uint32_t lws, std::string &err)
     return v_gemm_common(a, gws, lws, 4, err);
 }
 
-uint64_t grain_rows(const KArgs &a, uint64_t, uint32_t) { return (uint64_t)((a.i32(4) + BN - 1) / BN); }
+// Packages of whole pairs of tile rows: a chunk (two vertically adjacent
+// tiles) never straddles two packages.
+uint64_t grain_rows(const KArgs &a, uint64_t, uint32_t) { return (uint64_t)PAIR * ((a.i32(4) + BN - 1) / BN); }
+
+uint32_t nchunks_pairs(const KArgs &a, uint64_t, uint32_t, uint64_t off, uint64_t len)
+{
+    const int64_t tm = (a.i32(3) + BM - 1) / BM, tn = (a.i32(4) + BN - 1) / BN;
+    return gemm_chunks(2 * (tm / PAIR) * tn, off, len);
+}
 
 uint32_t nchunks_tiles(const KArgs &, uint64_t, uint32_t, uint64_t, uint64_t len) { return (uint32_t)len; }
 
@@ -450,7 +515,9 @@ ecl_status launch_main(const Maps &maps, const KArgs &a, const SchedArgs &s, con
     p.tiles_n = (p.N + BN - 1) / BN;
     p.kblocks = (uint32_t)((p.K + BK - 1) / BK);
     p.sweeps = sweeps;
-    p.order = tile_order((p.M + BM - 1) / BM, p.tiles_n, c.grid, (double)BM, (double)BN);  // strips of equal K
+    // tile pairs numbered in column groups over the grid of full CM-row pairs
+    p.tmf = ((p.M + BM - 1) / BM) / PAIR;
+    p.order = tile_order(p.tmf > 0 ? p.tmf : 1, p.tiles_n, c.grid, (double)CM, (double)BN);  // strips of equal K
     k_gemm<<<c.grid, NTHREADS, SMEM_BYTES, c.stream>>>(maps, p, s);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
@@ -464,7 +531,7 @@ ecl_status l_bf16(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
 {
     const int64_t M = a.i32(3), N = a.i32(4), K = a.i32(5);
     Maps maps;
-    if (!make_map(&maps.a[0], a.ptr[0], M, K, BM, err) || !make_map(&maps.b[0], a.ptr[1], N, K, BN, err))
+    if (!make_map(&maps.a[0], a.ptr[0], M, K, CM, err) || !make_map(&maps.b[0], a.ptr[1], N, K, BN, err))
         return ECL_ERR_CUDA;
     maps.a[1] = maps.a[0];
     maps.b[1] = maps.b[0];
@@ -492,7 +559,7 @@ ecl_status l_split(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::
     }
     mark_main_begin(c);
     Maps maps;
-    if (!make_map(&maps.a[0], ah, M, K, BM, err) || !make_map(&maps.a[1], alo, M, K, BM, err) ||
+    if (!make_map(&maps.a[0], ah, M, K, CM, err) || !make_map(&maps.a[1], alo, M, K, CM, err) ||
         !make_map(&maps.b[0], bh, N, K, BN, err) || !make_map(&maps.b[1], blo, N, K, BN, err))
         return ECL_ERR_CUDA;
     return launch_main(maps, a, s, c, 3, err);
@@ -550,13 +617,13 @@ ecl_status l_cast(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
 extern const KernelDesc kGemmBF16 = {
     "gemm_bf16", 6,
     {{"A", A_BUF_IN}, {"Bt", A_BUF_IN}, {"C", A_BUF_OUT}, {"M", A_I32}, {"N", A_I32}, {"K", A_I32}},
-    1, 1, NTHREADS, 4, v_bf16, grain_rows, nchunks_tiles, gemm_ctas_per_sm, l_bf16, true,
+    1, 1, NTHREADS, 4, v_bf16, grain_rows, nchunks_pairs, gemm_ctas_per_sm, l_bf16, true,
 };
 
 extern const KernelDesc kGemmSplit3 = {
     "gemm_split3", 6,
     {{"A", A_BUF_IN}, {"Bt", A_BUF_IN}, {"C", A_BUF_OUT}, {"M", A_I32}, {"N", A_I32}, {"K", A_I32}},
-    1, 1, NTHREADS, 4, v_split, grain_rows, nchunks_tiles, gemm_ctas_per_sm, l_split, true,
+    1, 1, NTHREADS, 4, v_split, grain_rows, nchunks_pairs, gemm_ctas_per_sm, l_split, true,
 };
 
 extern const KernelDesc kCastBF16 = {
