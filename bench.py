@@ -539,7 +539,9 @@ class Gemm(Workload):
         self.gws = self.tiles * self.lws
         self.lws6 = 128 * 128
         self.gws6 = (self.M // 128) * (self.N // 128) * self.lws6
-        self.config = dict(M=self.M, N=self.N, K=self.K, tile="128x256x64", scheduler="hguided k=2 over 4 devices",
+        self.config = dict(M=self.M, N=self.N, K=self.K, tile="128x256x64 work-groups, computed in vertical pairs",
+                           scheduler="hguided, packages of 128-row tiles (pairs of tile rows); k, minimum package and "
+                                     "devices autotuned for gemm_bf16 and gemm_split3 (k=2 over 4 devices otherwise)",
                            programs="gemm_bf16 (bf16 inputs) + gemm_split3 (fp32 inputs, 3 products) + "
                                     "gemm_split6 (fp32 inputs, 6 products, FP32 promotion every 64 of K, 128x128 tiles)")
 
@@ -581,6 +583,16 @@ class Gemm(Workload):
 
     def work_items(self):
         return 2 * self.M * self.N
+
+    def tunable(self, name):
+        # the step's two products: HGuided's devices, k and minimum package are searched
+        if name not in ("gemm_bf16", "gemm_split3"):
+            return None
+        ab, bb, af, bf = self.d_in
+        c = self.d_out[0] if name == "gemm_bf16" else self.d_out[1]
+        a, b = (ab, bb) if name == "gemm_bf16" else (af, bf)
+        return (lambda: self.E.Program(name).in_(a).in_(b).out(c).args(a, b, c, self.M, self.N, self.K),
+                self.gws, self.lws)
 
     def alg(self, name):
         f = 2.0 * self.M * self.N * self.K
