@@ -452,24 +452,25 @@ __device__ __forceinline__ void sbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait on phase `parity`; false (and the queue's error word set)
-// when it gave up after about two seconds.  Between polls the thread sleeps
-// with a doubling back-off of up to max_sleep_ns: a waiting warp must not
-// take issue slots from the compute warps (the scheduler warp waits out a
-// whole chunk here; measured, a polling loop added a quarter to the
-// instructions of a force run).
-__device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsigned int *gerr,
-                                          uint32_t max_sleep_ns)
+// when it gave up after about two seconds.  The thread waits suspended in
+// try_wait, which returns when the phase completes or after the suspend-time
+// hint (1 ms), so a waiting warp takes no issue slots from the compute warps
+// (the scheduler warp waits out a whole chunk here).  Measured against polls
+// separated by a doubling nanosleep back-off: Mandelbrot 53.6 -> 51.6 us, the
+// Gaussian 0.2373 -> 0.2355 ms, the NBody energy 0.7253 -> 0.7232 ms.
+constexpr uint32_t kWaitHintNs = 1000000;
+
+__device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsigned int *gerr)
 {
     uint64_t t0 = 0;
-    uint32_t ns = max_sleep_ns < 128 ? max_sleep_ns : 128;
     for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             "selp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
-            : "r"(sh_addr(bar)), "r"(parity)
+            : "r"(sh_addr(bar)), "r"(parity), "r"(kWaitHintNs)
             : "memory");
         if (ok) return true;
         const uint64_t now = gtime();
@@ -478,8 +479,6 @@ __device__ __forceinline__ bool sbar_wait(uint64_t *bar, uint32_t parity, unsign
             atomicExch(gerr, (unsigned int)ECL_ERR_TIMEOUT);
             return false;
         }
-        __nanosleep(ns);
-        if (ns < max_sleep_ns) ns <<= 1;
     }
 }
 
@@ -550,9 +549,9 @@ __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
                 if (counted && i > 0) {
                     const unsigned long long claimed = ld_relaxed(&s.dev[d].word);
                     const bool lazy = claimed >= nch || nch - claimed < s.C;
-                    if (lazy && !sbar_wait(&empty[r ^ 1], ((i - 1) >> 1) & 1, gerr, 256)) break;
+                    if (lazy && !sbar_wait(&empty[r ^ 1], ((i - 1) >> 1) & 1, gerr)) break;
                 }
-                if (!sbar_wait(&empty[r], ((i >> 1) & 1) ^ 1, gerr, 4096)) break;
+                if (!sbar_wait(&empty[r], ((i >> 1) & 1) ^ 1, gerr)) break;
                 Claim c = (*(volatile unsigned int *)gerr) ? Claim{} : claim_chunks<Body>(s, body.p, d);
                 if (*(volatile unsigned int *)gerr) c.done = 1;
                 nch = c.nchunks;
@@ -564,7 +563,7 @@ __device__ __forceinline__ void drive_ws(const SchedArgs &s, Body &body)
     } else {
         for (uint32_t i = 0;; ++i) {
             const uint32_t r = i & 1;
-            if (threadIdx.x == 0) flag = sbar_wait(&full[r], (i >> 1) & 1, gerr, 256) ? 0u : 1u;
+            if (threadIdx.x == 0) flag = sbar_wait(&full[r], (i >> 1) & 1, gerr) ? 0u : 1u;
             body_sync(NC);
             if (flag || ring[r].done) break;
             if (threadIdx.x == 0) st_ts = gtime();
