@@ -115,6 +115,10 @@ class Workload:
         """(fresh-program factory, gws, lws) of a program the autotuner may search, or None."""
         return None
 
+    def host_halves(self):
+        """Two host-buffer engines over the two halves of the work, or None."""
+        return None
+
     def programs(self):
         """(name, engine, work-items) of every program the step runs."""
         if isinstance(self.eng, MultiEngine):
@@ -438,6 +442,25 @@ class Binomial(Workload):
         eng.work_items(self.gws, self.lws).scheduler(s, prm).workers(D, C)
         eng.program(self.program(self.d_in, self.d_out, greeks=False))
         return eng
+
+    def host_halves(self):
+        """Host-buffer engines over options [0, n/2) and [n/2, n) (views of the
+        pinned buffers), so that another stage's copies can run during each."""
+        E = self.E
+        s, prm, D, C = self.sched
+        engs = []
+        for lo, hi in ((0, self.n // 2), (self.n // 2, self.n)):
+            ins = [t[lo:hi] for t in self.h_in]
+            price, gr = self.h_out[0][lo:hi], self.h_out[1][lo:hi]
+            p = E.Program("binomial")
+            for t in ins:
+                p.in_(t)
+            p.out(price).out(gr)
+            p.args(*ins, self.o["r"], hi - lo, price, gr)
+            eng = E.Engine(0)
+            eng.work_items((hi - lo) * 32, 32).scheduler(s, prm).workers(D, C).program(p)
+            engs.append(eng)
+        return engs
 
     def batched_report(self, timed):
         """The same options as 64 batches of uneven size: 64 launches (plain)
@@ -1023,7 +1046,21 @@ def run_ours(args):
         return x.engs if isinstance(x, MultiEngine) else [x]
 
     first = max(swls, key=dev_ms)
-    order = [first] + sorted((w for w in swls if w is not first), key=out_bytes, reverse=True)
+    rest = sorted((w for w in swls if w is not first), key=out_bytes, reverse=True)
+    order = [first] + rest
+    # the asynchronous pass: the longest stage's batch as two halves when it can
+    # be split, the stages with large results between them, so that those
+    # results move to the host while the second half computes (one copy stream
+    # each way is first-in first-out: a result queued behind the longest
+    # stage's would wait for it)
+    halves = first.host_halves()
+    big_out = [w for w in rest if out_bytes(w) >= (64 << 20)]
+    if halves is not None:
+        stages = ([("%s[0:n/2]" % first.name, [halves[0]])] + [(w.name, engines_of(w.host)) for w in big_out] +
+                  [("%s[n/2:n]" % first.name, [halves[1]])] +
+                  [(w.name, engines_of(w.host)) for w in rest if w not in big_out])
+    else:
+        stages = [(w.name, engines_of(w.host)) for w in order]
     for _ in range(max(1, args.warmup)):
         for w in swls:
             w.host.run()
@@ -1057,15 +1094,16 @@ def run_ours(args):
     e2e_sync_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
 
     copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
-    for w in order:
-        for e in engines_of(w.host):
+    for _, es in stages:
+        for e in es:
             e.copy_streams(copy_in, copy_out, asynchronous=True)
 
     def e2e_step():
-        for w in order:
-            w.host.run()  # enqueues copies in, the launch and copies out; returns at once
-        for w in order:
-            for e in engines_of(w.host):
+        for _, es in stages:
+            for e in es:
+                e.run()  # enqueues copies in, the launch and copies out; returns at once
+        for _, es in stages:
+            for e in es:
                 e.synchronize()  # this step's results are in host memory
 
     for _ in range(max(1, args.warmup)):
@@ -1110,8 +1148,9 @@ def run_ours(args):
         "e2e": {"value": job_rate(total_wi, world, e2e_s), "unit": "work-items/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
                 "how": "C ABI, host buffers: ecl_engine_copy_streams (copies on two copy streams, "
-                       "event-ordered around each launch, asynchronous runs); one synchronize per engine ends "
-                       "each step", "stage_order": [w.name for w in order]},
+                       "event-ordered around each launch, asynchronous runs); the longest stage's batch as two "
+                       "halves with the large-result stages between them; one synchronize per engine ends "
+                       "each step", "stage_order": [n for n, _ in stages]},
         "e2e_sync": {"value": job_rate(total_wi, world, e2e_sync_s), "unit": "work-items/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_sync_s * 1e3,
                      "how": "C ABI, host buffers: each run copies in, computes, copies out, then returns",
@@ -1132,6 +1171,8 @@ def run_ours(args):
         w.eng.close()
         w.mono.close()
         w.host.close()
+    for e in halves or []:
+        e.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
