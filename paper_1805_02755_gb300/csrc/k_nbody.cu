@@ -9,18 +9,18 @@
 //   nbody_fd       central differences of E in sampled coordinates
 //
 // The CTA has 256 threads.  Force kernels: a work-group of lws bodies (lws
-// 32..256, a power of two) is cut into S j-segments (whole 256-body tiles),
+// 32..256, a power of two) is cut into S j-segments (whole 512-body tiles),
 // one chunk each, so that a run has enough chunks to balance the persistent
 // CTAs; each chunk writes its per-body partial sums to the workspace and the
 // last chunk of the work-group (a counter per work-group) adds the S
 // partials in segment order and writes the result.  Within a chunk, thread
 // t owns two bodies of the work-group (t % (lws/2) and that + lws/2,
 // computed together in packed FP32x2 arithmetic) and the j-slice
-// t / (lws/2).  Energy: thread t owns
-// body t % lws and the j-slice t / lws.  j-bodies are staged in shared
-// memory 256 at a time (tiles on an absolute 256-body grid).  Each thread sums the pair terms of
-// one tile in FP32, then adds the tile sum to its running FP32 total
-// (two-level summation); the slices of a body are added in slice order.
+// t / (lws/2).  Energy: thread t owns body t % lws and the j-slice t / lws.
+// j-bodies are staged in shared memory 512 (force) or 256 (energy) at a time,
+// tiles on an absolute grid.  Each thread sums the pair terms of one tile in
+// FP32, then adds the tile sum to its running FP32 total (two-level
+// summation); the slices of a body are added in slice order.
 // The energy and finite-difference sums are FP32 pair terms accumulated in
 // FP64, reduced in a fixed order, so results do not depend on scheduling.
 #include <cuda_runtime.h>
@@ -37,7 +37,13 @@ namespace {
 constexpr int kBlock = 256;   // energy and finite-difference CTAs
 constexpr int kTile = 256;
 constexpr int kFBlock = 256;  // force CTA: 8 compute warps (+ the scheduler warp), 3 per SM
-constexpr int kFTile = 256;   // j-bodies per staged force tile
+// j-bodies per staged force tile: a thread's j-slice of a tile is 2 lws/2
+// bodies, so that the persistent form's per-tile call (see pair_tile_call)
+// is paid once per 64 pairs at lws 64.  Measured at 65536 bodies against
+// 256-body tiles: force 1.862 -> 1.812 ms, adjoint 1.975 -> 1.900 ms (1024:
+// 1.790 / 1.965 ms).
+constexpr int kFTile = 512;
+constexpr int kFStage = kFTile / kFBlock;  // j-bodies each thread stages per tile
 // Force shared memory: two duplicated tiles (x,x,y,y) and (z,z,m,m), double
 // buffered (the slice partials reuse the first half after the tile loop),
 // then each thread's running totals (a_x, a_y, a_z, potential) of its two
@@ -83,18 +89,18 @@ __device__ __forceinline__ void stage_tile(float4 *sh, const float4 *pos, int64_
     sh[threadIdx.x] = (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// j-body `tile * kFTile + threadIdx.x` (zero-mass padding beyond n).
-__device__ __forceinline__ float4 tile_body(const float4 *pos, int64_t n, int64_t tile)
+// j-body `tile * kFTile + h * kFBlock + threadIdx.x` (zero-mass padding beyond n).
+__device__ __forceinline__ float4 tile_body(const float4 *pos, int64_t n, int64_t tile, int h)
 {
-    const int64_t j = tile * kFTile + threadIdx.x;
+    const int64_t j = tile * kFTile + h * kFBlock + threadIdx.x;
     return (j < n) ? __ldg(pos + j) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Store one j-body duplicated for packed use: (x,x,y,y) and (z,z,m,m).
-__device__ __forceinline__ void put_dup(float4 *shxy, float4 *shzm, const float4 &q)
+__device__ __forceinline__ void put_dup(float4 *shxy, float4 *shzm, const float4 &q, int h)
 {
-    shxy[threadIdx.x] = make_float4(q.x, q.x, q.y, q.y);
-    shzm[threadIdx.x] = make_float4(q.z, q.z, q.w, q.w);
+    shxy[h * kFBlock + threadIdx.x] = make_float4(q.x, q.x, q.y, q.y);
+    shzm[h * kFBlock + threadIdx.x] = make_float4(q.z, q.z, q.w, q.w);
 }
 
 // The pair loop over one tile's j-slice for a thread's two bodies: sums of
@@ -192,13 +198,18 @@ struct ForceBody {
         A[2 * kFBlock] = 0;
         if (MODE == NB_ADJ) A[3 * kFBlock] = 0;
         body_sync(kFBlock);  // the previous chunk is done with both buffers
-        if (ta < tb) put_dup(shxy, shzm, tile_body(p.pos, p.n, ta));
+        if (ta < tb) {
+#pragma unroll
+            for (int h = 0; h < kFStage; ++h) put_dup(shxy, shzm, tile_body(p.pos, p.n, ta, h), h);
+        }
         body_sync(kFBlock);
         for (int64_t tile = ta; tile < tb; ++tile) {
             const uint32_t cur = (uint32_t)(tile - ta) & 1u;
             const bool more = tile + 1 < tb;
-            float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (more) nxt = tile_body(p.pos, p.n, tile + 1);
+            float4 nxt[kFStage];
+#pragma unroll
+            for (int h = 0; h < kFStage; ++h)
+                nxt[h] = more ? tile_body(p.pos, p.n, tile + 1, h) : make_float4(0.f, 0.f, 0.f, 0.f);
             const ulonglong2 *qxy = reinterpret_cast<const ulonglong2 *>(shxy + cur * kFTile + s * SPAN);
             const ulonglong2 *qzm = reinterpret_cast<const ulonglong2 *>(shzm + cur * kFTile + s * SPAN);
             const TileSums T = CALL ? pair_tile_call<MODE, SPAN>(qxy, qzm, X, Y, Z, EPS)
@@ -209,7 +220,11 @@ struct ForceBody {
             A[2 * kFBlock] = add2(A[2 * kFBlock], TZ);
             if (MODE == NB_ADJ) A[3 * kFBlock] = add2(A[3 * kFBlock], TP);
             // the other buffer was last read before the previous barrier
-            if (more) put_dup(shxy + (cur ^ 1u) * kFTile, shzm + (cur ^ 1u) * kFTile, nxt);
+            if (more) {
+#pragma unroll
+                for (int h = 0; h < kFStage; ++h)
+                    put_dup(shxy + (cur ^ 1u) * kFTile, shzm + (cur ^ 1u) * kFTile, nxt[h], h);
+            }
             body_sync(kFBlock);
         }
     }
@@ -229,13 +244,14 @@ struct ForceBody {
         const f2 EPS = pk(p.eps2, p.eps2);
         const int64_t ntiles = (p.n + kFTile - 1) / kFTile;
         const int64_t ta = ntiles * sg / p.seg, tb = ntiles * (sg + 1) / p.seg;
-        // the j-slice length kFTile / S equals half: one instance of the
-        // tile loop per lws, so that the pair loop's trip count is a constant
+        // the j-slice length kFTile / S equals kFStage * half: one instance
+        // of the tile loop per lws, so that the pair loop's trip count is a
+        // constant
         switch (half) {
-        case 16: tiles<16>(ta, tb, s, X, Y, Z, EPS); break;
-        case 32: tiles<32>(ta, tb, s, X, Y, Z, EPS); break;
-        case 64: tiles<64>(ta, tb, s, X, Y, Z, EPS); break;
-        default: tiles<128>(ta, tb, s, X, Y, Z, EPS); break;
+        case 16: tiles<16 * kFStage>(ta, tb, s, X, Y, Z, EPS); break;
+        case 32: tiles<32 * kFStage>(ta, tb, s, X, Y, Z, EPS); break;
+        case 64: tiles<64 * kFStage>(ta, tb, s, X, Y, Z, EPS); break;
+        default: tiles<128 * kFStage>(ta, tb, s, X, Y, Z, EPS); break;
         }
         // combine the slices of each body in slice order
         float ax0, ax1, ay0, ay1, az0, az1, pt0 = 0.f, pt1 = 0.f;
