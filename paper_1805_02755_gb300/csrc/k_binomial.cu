@@ -539,9 +539,13 @@ __device__ __forceinline__ Opt make_opt(float S, float K, float T, float sig, in
     return op;
 }
 
-// Delta and the vega leaf part of one option from the closed-form adjoint
-// weights, summed over the warp (every lane gets the sums).
-__device__ __forceinline__ float2 closed_form_greeks(const Opt &op, int nz, int lane)
+// The per-option constants of the closed-form greeks' leaf sums: the high
+// and low parts of C (see below) and the FP32 pair L.
+struct GreeksConsts {
+    float Ch, Cl, Lx, Ly;
+};
+
+__device__ __forceinline__ GreeksConsts greeks_consts(const Opt &op)
 {
     // stored leaf i's weight in the root is the binomial pmf
     // C(N,i) w^i (1-w)^(N-i), w = (1 + v)/2 with v the lattice's own FP32
@@ -579,32 +583,60 @@ __device__ __forceinline__ float2 closed_form_greeks(const Opt &op, int nz, int 
     // < 88 keeps the leaves finite).  The low parts (each below 2^-10)
     // are added in FP32, and the exponential of the exact high sum is
     // corrected by (1 + low sum).
-    const float Ch = rintf(C.x * 1024.f) * (1.0f / 1024.f);
-    const float Cl = (C.x - Ch) + C.y;
+    GreeksConsts k;
+    k.Ch = rintf(C.x * 1024.f) * (1.0f / 1024.f);
+    k.Cl = (C.x - k.Ch) + C.y;
+    k.Lx = L.x;
+    k.Ly = L.y;
+    return k;
+}
+
+// This lane's part of the two leaf sums of an option with N steps and nz
+// in-the-money leaves (leaves lane, lane + 32, ...), scaled by sgn and fv.
+__device__ __forceinline__ float2 greeks_leaf_sums(const GreeksConsts &k, int N, int nz, float sgn, float fv, int lane)
+{
     float sd = 0.f, sv = 0.f;
 #pragma unroll 2
     for (int i = lane; i < nz; i += kWarp) {
-        const float2 x = g_lfact[i], y = g_lfact[op.N - i];
+        const float2 x = g_lfact[i], y = g_lfact[N - i];
         const float fi = (float)i;
-        const float pr = fi * L.x;
+        const float pr = fi * k.Lx;
         const float ph = rintf(pr * 1024.f) * (1.0f / 1024.f);
-        const float pl = (pr - ph) + fmaf(fi, L.y, fmaf(fi, L.x, -pr));
-        const float h = ((Ch - x.x) - y.x) + ph;
-        const float lo = ((Cl - x.y) - y.y) + pl;
+        const float pl = (pr - ph) + fmaf(fi, k.Ly, fmaf(fi, k.Lx, -pr));
+        const float h = ((k.Ch - x.x) - y.x) + ph;
+        const float lo = ((k.Cl - x.y) - y.y) + pl;
         const float e = expf(h);
         const float wg = fmaf(e, lo, e);
         sd += wg;
-        sv = fmaf(wg, (float)(2 * i - op.N), sv);
+        sv = fmaf(wg, (float)(2 * i - N), sv);
     }
-    const float sgn = op.put ? -1.f : 1.f;
-    sd *= sgn;
-    sv *= (op.refl ? -sgn : sgn) * op.S * op.sdt;
+    return make_float2(sd * sgn, sv * fv);
+}
+
+__device__ __forceinline__ float2 warp_sum2(float2 v)
+{
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
-        sd += __shfl_xor_sync(kFull, sd, o2);
-        sv += __shfl_xor_sync(kFull, sv, o2);
+        v.x += __shfl_xor_sync(kFull, v.x, o2);
+        v.y += __shfl_xor_sync(kFull, v.y, o2);
     }
-    return make_float2(sd, sv);
+    return v;
+}
+
+// The vega sum's factor: dS_T/dsigma = S g m sqrt(dt), m in storage order
+// (negated when reflected), both sums negated on the put side.
+__device__ __forceinline__ float vega_factor(const Opt &op)
+{
+    const float sgn = op.put ? -1.f : 1.f;
+    return (op.refl ? -sgn : sgn) * op.S * op.sdt;
+}
+
+// Delta and the vega leaf part of one option from the closed-form adjoint
+// weights, summed over the warp (every lane gets the sums).
+__device__ __forceinline__ float2 closed_form_greeks(const Opt &op, int nz, int lane)
+{
+    const GreeksConsts k = greeks_consts(op);
+    return warp_sum2(greeks_leaf_sums(k, op.N, nz, op.put ? -1.f : 1.f, vega_factor(op), lane));
 }
 
 // The greeks of the banded form in two launches: the lattice kernel leaves
@@ -757,13 +789,66 @@ __global__ void __launch_bounds__(kWarp, FULL ? kMinCtasFull : kMinCtas) k_binom
 }
 
 // The banded form's greeks pass: a plain launch after the lattice kernel on
-// the same stream, one warp per option (8 per CTA).
+// the same stream, 32 options per warp (8 warps per CTA).  Each lane sets up
+// one option (its CRR values and the leaf sums' constants: a few hundred
+// instructions that a warp per option computed 32 times over), then the
+// warp sums each option's leaves in turn, with the same arithmetic and in
+// the same order as greeks_option, and each lane finishes its own option.
 constexpr int kGreeksWarps = 8;
 
 __global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoParams p)
 {
-    const int64_t o = (int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp;
-    if (o < p.n) greeks_option(p, o);
+    const float kNaN = __int_as_float(0x7fc00000);
+    const int lane = threadIdx.x & 31;
+    const int64_t o = ((int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp) * kWarp + lane;
+    // this lane's option: its scratch pair and constants
+    bool ok = false;
+    int N = 0, nz = 0;
+    float d1v = 0.f, T = 0.f, sgn = 1.f, fv = 0.f;
+    Crr c{};
+    GreeksConsts k{};
+    bool put = false;
+    if (o < p.n) {
+        N = __ldg(p.steps + o);
+        const float2 sc = p.greeks[o];
+        nz = __float_as_int(sc.x);
+        d1v = sc.y;
+        // nz outside 0..N+1: a marked option, or a scratch pair that no
+        // lattice wrote (a run that ended with an error): NaN, nothing indexed
+        ok = !(N < 1 || N > kMaxSteps || nz < 0 || nz > N + 1);
+        if (ok) {
+            T = __ldg(p.T + o);
+            const Opt op = make_opt<false>(__ldg(p.S + o), __ldg(p.K + o), T, __ldg(p.sigma + o), N, p.r, c);
+            k = greeks_consts(op);
+            put = op.put;
+            sgn = op.put ? -1.f : 1.f;
+            fv = vega_factor(op);
+        }
+    }
+    // the warp sums the leaves of each valid option of its 32
+    float2 mine = make_float2(0.f, 0.f);
+    for (int j = 0; j < kWarp; ++j) {
+        if (!__shfl_sync(kFull, (int)ok, j)) continue;  // warp-uniform
+        GreeksConsts kj;
+        kj.Ch = __shfl_sync(kFull, k.Ch, j);
+        kj.Cl = __shfl_sync(kFull, k.Cl, j);
+        kj.Lx = __shfl_sync(kFull, k.Lx, j);
+        kj.Ly = __shfl_sync(kFull, k.Ly, j);
+        const int Nj = __shfl_sync(kFull, N, j), nzj = __shfl_sync(kFull, nz, j);
+        const float sgnj = __shfl_sync(kFull, sgn, j), fvj = __shfl_sync(kFull, fv, j);
+        const float2 dv = warp_sum2(greeks_leaf_sums(kj, Nj, nzj, sgnj, fvj, lane));
+        if (lane == j) mine = dv;
+    }
+    if (o >= p.n) return;
+    if (!ok) {
+        p.greeks[o] = make_float2(kNaN, kNaN);
+        return;
+    }
+    const float disc = expf(-p.r * T);
+    const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
+    float delta = mine.x * disc;
+    if (put) delta += 1.0f;
+    p.greeks[o] = make_float2(delta, fmaf((float)N * q2p, d1v, mine.y * disc));
 }
 
 // ---------------------------------------------------------------- batches
@@ -912,7 +997,8 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     k_binomial<FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
     mark_main_end(c);
     if (!FULL && p.greeks && p.n > 0)
-        k_binomial_greeks<<<(unsigned)((p.n + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0, c.stream>>>(p);
+        k_binomial_greeks<<<(unsigned)((p.n + kGreeksWarps * kWarp - 1) / (kGreeksWarps * kWarp)),
+                            kWarp * kGreeksWarps, 0, c.stream>>>(p);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);

@@ -65,6 +65,37 @@ def test_uneven_batches_one_launch(E, oracle_mod):
     bb.close()
 
 
+def test_batched_greeks_equal_the_single_launch_bit_for_bit(E):
+    # The single launch's greeks pass sets up 32 options per warp (one per
+    # lane) and sums each option's leaves in turn; the batched pass runs one
+    # warp per option.  Both take the same arithmetic in the same order, so
+    # prices and greeks agree bit for bit, including a ragged last warp and
+    # options of a single step.
+    import torch
+    from paper_1805_02755_gb300.batching import BinomialBatch
+    n = 1037
+    b = make_batches(torch, [n], 830)[0]
+    b["steps"][:3] = 1
+    b["steps"][3:6] = 2048  # the deepest lattice
+    bb = BinomialBatch([b], with_greeks=True)
+    bb.run()
+    torch.cuda.synchronize()
+    bb.close()
+    price = torch.full((n,), -2.0, device="cuda")
+    gr = torch.full((n, 2), -2.0, device="cuda")
+    eng = E.Engine(0)
+    prog = E.Program("binomial")
+    for k in ("S", "K", "T", "sigma", "steps"):
+        prog.in_(b[k])
+    prog.out(price).out(gr)
+    prog.args(b["S"], b["K"], b["T"], b["sigma"], b["steps"], b["r"], n, price, gr)
+    eng.work_items(n * 32, 32).scheduler("hguided", (2.0, 1.0)).workers(8, 0).program(prog)
+    eng.run().synchronize()
+    eng.close()
+    assert torch.equal(price, b["price"])
+    assert torch.equal(gr, b["greeks"])
+
+
 def test_batches_with_and_without_greeks_arrays_in_one_launch(E, oracle_mod):
     # The greeks of a batch come from a pass after the lattice kernel, which
     # reads what the lattice left in each instance's greeks array: instances
