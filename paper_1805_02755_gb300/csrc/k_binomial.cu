@@ -789,18 +789,21 @@ __global__ void __launch_bounds__(kWarp, FULL ? kMinCtasFull : kMinCtas) k_binom
 }
 
 // The banded form's greeks pass: a plain launch after the lattice kernel on
-// the same stream, 32 options per warp (8 warps per CTA).  Each lane sets up
-// one option (its CRR values and the leaf sums' constants: a few hundred
-// instructions that a warp per option computed 32 times over), then the
-// warp sums each option's leaves in turn, with the same arithmetic and in
-// the same order as greeks_option, and each lane finishes its own option.
+// the same stream, `per` (1..32) options per warp, 8 warps per CTA.  Lane l
+// < per sets up option l of its warp (its CRR values and the leaf sums'
+// constants: a few hundred instructions that a warp per option computed 32
+// times over), then the warp sums each option's leaves in turn, with the
+// same arithmetic and in the same order as greeks_option, and each lane
+// finishes its own option.  The launcher picks per so that the warps still
+// fill the GPU (32 for 2^20 options; 2 for 16384).
 constexpr int kGreeksWarps = 8;
 
-__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoParams p)
+__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoParams p, int per)
 {
     const float kNaN = __int_as_float(0x7fc00000);
     const int lane = threadIdx.x & 31;
-    const int64_t o = ((int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp) * kWarp + lane;
+    const int64_t o = ((int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp) * per + lane;
+    const bool mine = lane < per && o < p.n;
     // this lane's option: its scratch pair and constants
     bool ok = false;
     int N = 0, nz = 0;
@@ -808,7 +811,7 @@ __global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoPa
     Crr c{};
     GreeksConsts k{};
     bool put = false;
-    if (o < p.n) {
+    if (mine) {
         N = __ldg(p.steps + o);
         const float2 sc = p.greeks[o];
         nz = __float_as_int(sc.x);
@@ -826,8 +829,8 @@ __global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoPa
         }
     }
     // the warp sums the leaves of each valid option of its 32
-    float2 mine = make_float2(0.f, 0.f);
-    for (int j = 0; j < kWarp; ++j) {
+    float2 sums = make_float2(0.f, 0.f);
+    for (int j = 0; j < per; ++j) {
         if (!__shfl_sync(kFull, (int)ok, j)) continue;  // warp-uniform
         GreeksConsts kj;
         kj.Ch = __shfl_sync(kFull, k.Ch, j);
@@ -837,18 +840,18 @@ __global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoPa
         const int Nj = __shfl_sync(kFull, N, j), nzj = __shfl_sync(kFull, nz, j);
         const float sgnj = __shfl_sync(kFull, sgn, j), fvj = __shfl_sync(kFull, fv, j);
         const float2 dv = warp_sum2(greeks_leaf_sums(kj, Nj, nzj, sgnj, fvj, lane));
-        if (lane == j) mine = dv;
+        if (lane == j) sums = dv;
     }
-    if (o >= p.n) return;
+    if (!mine) return;
     if (!ok) {
         p.greeks[o] = make_float2(kNaN, kNaN);
         return;
     }
     const float disc = expf(-p.r * T);
     const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
-    float delta = mine.x * disc;
+    float delta = sums.x * disc;
     if (put) delta += 1.0f;
-    p.greeks[o] = make_float2(delta, fmaf((float)N * q2p, d1v, mine.y * disc));
+    p.greeks[o] = make_float2(delta, fmaf((float)N * q2p, d1v, sums.y * disc));
 }
 
 // ---------------------------------------------------------------- batches
@@ -934,6 +937,26 @@ __global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_batch_greeks(
         greeks_option(bp, local);
 }
 
+// Options per warp of the greeks pass: as many as keep every resident warp
+// slot of the GPU busy, at most 32.
+int greeks_per_warp(int64_t n)
+{
+    static int slots = 0;  // resident warps of k_binomial_greeks on device 0
+    if (!slots) {
+        int sms = 0, ctas = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_binomial_greeks, kWarp * kGreeksWarps, 0) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            sms = 152;
+            ctas = 5;
+        }
+        slots = sms * ctas * kGreeksWarps;
+    }
+    const int64_t per = n / (slots > 0 ? slots : 1);
+    return (int)(per < 1 ? 1 : (per > kWarp ? kWarp : per));
+}
+
 int occ(const void *fn)
 {
     int n = 0;
@@ -996,9 +1019,12 @@ ecl_status launch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::s
     p.greeks = a.buf<float2>(8);
     k_binomial<FULL><<<c.grid, kWarp, 0, c.stream>>>(p, s);
     mark_main_end(c);
-    if (!FULL && p.greeks && p.n > 0)
-        k_binomial_greeks<<<(unsigned)((p.n + kGreeksWarps * kWarp - 1) / (kGreeksWarps * kWarp)),
-                            kWarp * kGreeksWarps, 0, c.stream>>>(p);
+    if (!FULL && p.greeks && p.n > 0) {
+        const int per = greeks_per_warp(p.n);
+        const int64_t warps = ((int64_t)p.n + per - 1) / per;
+        k_binomial_greeks<<<(unsigned)((warps + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0,
+                            c.stream>>>(p, per);
+    }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);

@@ -65,15 +65,15 @@ def test_uneven_batches_one_launch(E, oracle_mod):
     bb.close()
 
 
-def test_batched_greeks_equal_the_single_launch_bit_for_bit(E):
-    # The single launch's greeks pass sets up 32 options per warp (one per
-    # lane) and sums each option's leaves in turn; the batched pass runs one
-    # warp per option.  Both take the same arithmetic in the same order, so
-    # prices and greeks agree bit for bit, including a ragged last warp and
-    # options of a single step.
+@pytest.mark.parametrize("n", [1037, 200003])
+def test_batched_greeks_equal_the_single_launch_bit_for_bit(E, n):
+    # The single launch's greeks pass sets up several options per warp (one
+    # per lane: 1 at 1037 options, 32 at 200003) and sums each option's
+    # leaves in turn; the batched pass runs one warp per option.  Both take
+    # the same arithmetic in the same order, so prices and greeks agree bit
+    # for bit, including a ragged last warp and options of a single step.
     import torch
     from paper_1805_02755_gb300.batching import BinomialBatch
-    n = 1037
     b = make_batches(torch, [n], 830)[0]
     b["steps"][:3] = 1
     b["steps"][3:6] = 2048  # the deepest lattice
