@@ -730,37 +730,6 @@ __device__ __forceinline__ void price_option(const BinoParams &p, int64_t o, flo
     }
 }
 
-// Delta and vega of one option of the banded form from the scratch pair
-// its lattice left in greeks[o] (one warp): the closed-form sums over the
-// nz nonzero leaves (binomial probabilities, discounted), plus 1 for the
-// calls priced through the put, and the vega term through p.
-__device__ __forceinline__ void greeks_option(const BinoParams &p, int64_t o)
-{
-    const float kNaN = __int_as_float(0x7fc00000);
-    const int lane = threadIdx.x & 31;
-    const int N = __ldg(p.steps + o);
-    const float2 sc = p.greeks[o];
-    const int nz = __float_as_int(sc.x);
-    __syncwarp();  // every lane has read the scratch before lane 0 overwrites it
-    // nz outside 0..N+1: a marked option, or a scratch pair that no lattice
-    // wrote (a run that ended with an error): NaN, and nothing indexed by it
-    if (N < 1 || N > kMaxSteps || nz < 0 || nz > N + 1) {
-        if (lane == 0) p.greeks[o] = make_float2(kNaN, kNaN);
-        return;
-    }
-    const float T = __ldg(p.T + o);
-    Crr c;
-    const Opt op = make_opt<false>(__ldg(p.S + o), __ldg(p.K + o), T, __ldg(p.sigma + o), N, p.r, c);
-    const float2 dv = closed_form_greeks(op, nz, lane);
-    if (lane == 0) {
-        const float disc = expf(-p.r * T);
-        const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
-        float delta = dv.x * disc;
-        if (op.put) delta += 1.0f;
-        p.greeks[o] = make_float2(delta, fmaf((float)N * q2p, sc.y, dv.y * disc));
-    }
-}
-
 template <bool FULL>
 struct BinoBody {
     using Params = BinoParams;
@@ -792,66 +761,92 @@ __global__ void __launch_bounds__(kWarp, FULL ? kMinCtasFull : kMinCtas) k_binom
 // the same stream, `per` (1..32) options per warp, 8 warps per CTA.  Lane l
 // < per sets up option l of its warp (its CRR values and the leaf sums'
 // constants: a few hundred instructions that a warp per option computed 32
-// times over), then the warp sums each option's leaves in turn, with the
-// same arithmetic and in the same order as greeks_option, and each lane
-// finishes its own option.  The launcher picks per so that the warps still
+// times over), then the warp sums each option's leaves in turn (lane i of
+// the warp takes leaves i, i + 32, ..., and the warp adds the lanes' sums
+// in a fixed order), and each lane finishes its own option: delta and
+// vega from the closed-form sums over the nz nonzero leaves (binomial
+// probabilities, discounted), plus 1 for the calls priced through the put,
+// and the vega term through p that the lattice left in the scratch pair.
+// The batched launch takes the same path, so both agree bit for bit.  The launcher picks per so that the warps still
 // fill the GPU (32 for 2^20 options; 2 for 16384).
 constexpr int kGreeksWarps = 8;
 
-__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoParams p, int per)
+// One lane's option in the greeks pass.
+struct GreeksLane {
+    float2 *out;  // greeks[o] of the option, or nullptr: no option
+    bool ok;      // a valid scratch pair (else NaN results)
+    bool put;
+    int N, nz;
+    float d1v, T, r, sgn, fv;
+    Crr c;
+    GreeksConsts k;
+};
+
+// Reads option o's scratch pair and sets up its constants.
+__device__ __forceinline__ void greeks_lane_setup(GreeksLane &g, const BinoParams &p, int64_t o)
 {
-    const float kNaN = __int_as_float(0x7fc00000);
-    const int lane = threadIdx.x & 31;
-    const int64_t o = ((int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp) * per + lane;
-    const bool mine = lane < per && o < p.n;
-    // this lane's option: its scratch pair and constants
-    bool ok = false;
-    int N = 0, nz = 0;
-    float d1v = 0.f, T = 0.f, sgn = 1.f, fv = 0.f;
-    Crr c{};
-    GreeksConsts k{};
-    bool put = false;
-    if (mine) {
-        N = __ldg(p.steps + o);
-        const float2 sc = p.greeks[o];
-        nz = __float_as_int(sc.x);
-        d1v = sc.y;
-        // nz outside 0..N+1: a marked option, or a scratch pair that no
-        // lattice wrote (a run that ended with an error): NaN, nothing indexed
-        ok = !(N < 1 || N > kMaxSteps || nz < 0 || nz > N + 1);
-        if (ok) {
-            T = __ldg(p.T + o);
-            const Opt op = make_opt<false>(__ldg(p.S + o), __ldg(p.K + o), T, __ldg(p.sigma + o), N, p.r, c);
-            k = greeks_consts(op);
-            put = op.put;
-            sgn = op.put ? -1.f : 1.f;
-            fv = vega_factor(op);
-        }
+    g.out = p.greeks + o;
+    g.N = __ldg(p.steps + o);
+    const float2 sc = *g.out;
+    g.nz = __float_as_int(sc.x);
+    g.d1v = sc.y;
+    g.r = p.r;
+    // nz outside 0..N+1: a marked option, or a scratch pair that no lattice
+    // wrote (a run that ended with an error): NaN, nothing indexed by it
+    g.ok = !(g.N < 1 || g.N > kMaxSteps || g.nz < 0 || g.nz > g.N + 1);
+    if (g.ok) {
+        g.T = __ldg(p.T + o);
+        const Opt op = make_opt<false>(__ldg(p.S + o), __ldg(p.K + o), g.T, __ldg(p.sigma + o), g.N, p.r, g.c);
+        g.k = greeks_consts(op);
+        g.put = op.put;
+        g.sgn = op.put ? -1.f : 1.f;
+        g.fv = vega_factor(op);
     }
-    // the warp sums the leaves of each valid option of its 32
+}
+
+// The warp sums the leaves of the valid options of lanes 0..per-1 in turn;
+// each lane gets its own option's sums.
+__device__ __forceinline__ float2 greeks_warp_sums(const GreeksLane &g, int per, int lane)
+{
     float2 sums = make_float2(0.f, 0.f);
     for (int j = 0; j < per; ++j) {
-        if (!__shfl_sync(kFull, (int)ok, j)) continue;  // warp-uniform
+        if (!__shfl_sync(kFull, (int)g.ok, j)) continue;  // warp-uniform
         GreeksConsts kj;
-        kj.Ch = __shfl_sync(kFull, k.Ch, j);
-        kj.Cl = __shfl_sync(kFull, k.Cl, j);
-        kj.Lx = __shfl_sync(kFull, k.Lx, j);
-        kj.Ly = __shfl_sync(kFull, k.Ly, j);
-        const int Nj = __shfl_sync(kFull, N, j), nzj = __shfl_sync(kFull, nz, j);
-        const float sgnj = __shfl_sync(kFull, sgn, j), fvj = __shfl_sync(kFull, fv, j);
+        kj.Ch = __shfl_sync(kFull, g.k.Ch, j);
+        kj.Cl = __shfl_sync(kFull, g.k.Cl, j);
+        kj.Lx = __shfl_sync(kFull, g.k.Lx, j);
+        kj.Ly = __shfl_sync(kFull, g.k.Ly, j);
+        const int Nj = __shfl_sync(kFull, g.N, j), nzj = __shfl_sync(kFull, g.nz, j);
+        const float sgnj = __shfl_sync(kFull, g.sgn, j), fvj = __shfl_sync(kFull, g.fv, j);
         const float2 dv = warp_sum2(greeks_leaf_sums(kj, Nj, nzj, sgnj, fvj, lane));
         if (lane == j) sums = dv;
     }
-    if (!mine) return;
-    if (!ok) {
-        p.greeks[o] = make_float2(kNaN, kNaN);
+    return sums;
+}
+
+// (delta, vega) of the lane's option from its sums.
+__device__ __forceinline__ void greeks_lane_finish(const GreeksLane &g, float2 sums)
+{
+    const float kNaN = __int_as_float(0x7fc00000);
+    if (!g.ok) {
+        *g.out = make_float2(kNaN, kNaN);
         return;
     }
-    const float disc = expf(-p.r * T);
-    const float q2p = 2.0f * c.sdt * (-0.5f - c.q * (coshf(c.a) / c.s1));  // 2 dq/dsigma
+    const float disc = expf(-g.r * g.T);
+    const float q2p = 2.0f * g.c.sdt * (-0.5f - g.c.q * (coshf(g.c.a) / g.c.s1));  // 2 dq/dsigma
     float delta = sums.x * disc;
-    if (put) delta += 1.0f;
-    p.greeks[o] = make_float2(delta, fmaf((float)N * q2p, d1v, sums.y * disc));
+    if (g.put) delta += 1.0f;
+    *g.out = make_float2(delta, fmaf((float)g.N * q2p, g.d1v, sums.y * disc));
+}
+
+__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_greeks(BinoParams p, int per)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t o = ((int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp) * per + lane;
+    GreeksLane g{};
+    if (lane < per && o < p.n) greeks_lane_setup(g, p, o);
+    const float2 sums = greeks_warp_sums(g, per, lane);
+    if (g.out) greeks_lane_finish(g, sums);
 }
 
 // ---------------------------------------------------------------- batches
@@ -929,12 +924,16 @@ __global__ void __launch_bounds__(kWarp, kMinCtas) k_binomial_batch(BinoBatchPar
 }
 
 // The batch's greeks pass (instances with a greeks array), as for one batch.
-__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_batch_greeks(BinoBatchParams prm)
+__global__ void __launch_bounds__(kWarp * kGreeksWarps) k_binomial_batch_greeks(BinoBatchParams prm, int per)
 {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = ((int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp) * per + lane;
+    GreeksLane g{};
     BinoParams bp;
     int64_t local;
-    if (batch_option(prm, (int64_t)blockIdx.x * kGreeksWarps + threadIdx.x / kWarp, bp, local) && bp.greeks)
-        greeks_option(bp, local);
+    if (lane < per && batch_option(prm, o, bp, local) && bp.greeks) greeks_lane_setup(g, bp, local);
+    const float2 sums = greeks_warp_sums(g, per, lane);
+    if (g.out) greeks_lane_finish(g, sums);
 }
 
 // Options per warp of the greeks pass: as many as keep every resident warp
@@ -1067,9 +1066,12 @@ ecl_status l_batch(const KArgs &a, const SchedArgs &s, const LaunchCtx &c, std::
     p.greeks = a.i32(3) ? 1 : 0;
     k_binomial_batch<<<c.grid, kWarp, 0, c.stream>>>(p, s);
     mark_main_end(c);
-    if (p.greeks)
-        k_binomial_batch_greeks<<<(unsigned)((p.total + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0,
-                                  c.stream>>>(p);
+    if (p.greeks && p.total > 0) {
+        const int per = greeks_per_warp(p.total);
+        const int64_t warps = (p.total + per - 1) / per;
+        k_binomial_batch_greeks<<<(unsigned)((warps + kGreeksWarps - 1) / kGreeksWarps), kWarp * kGreeksWarps, 0,
+                                  c.stream>>>(p, per);
+    }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("launch: ") + cudaGetErrorString(ce);

@@ -65,35 +65,55 @@ def test_uneven_batches_one_launch(E, oracle_mod):
     bb.close()
 
 
-@pytest.mark.parametrize("n", [1037, 200003])
-def test_batched_greeks_equal_the_single_launch_bit_for_bit(E, n):
-    # The single launch's greeks pass sets up several options per warp (one
-    # per lane: 1 at 1037 options, 32 at 200003) and sums each option's
-    # leaves in turn; the batched pass runs one warp per option.  Both take
-    # the same arithmetic in the same order, so prices and greeks agree bit
-    # for bit, including a ragged last warp and options of a single step.
-    import torch
-    from paper_1805_02755_gb300.batching import BinomialBatch
-    b = make_batches(torch, [n], 830)[0]
-    b["steps"][:3] = 1
-    b["steps"][3:6] = 2048  # the deepest lattice
-    bb = BinomialBatch([b], with_greeks=True)
-    bb.run()
-    torch.cuda.synchronize()
-    bb.close()
+def _single_launch(E, torch, t, r):
+    n = t["S"].numel()
     price = torch.full((n,), -2.0, device="cuda")
     gr = torch.full((n, 2), -2.0, device="cuda")
     eng = E.Engine(0)
     prog = E.Program("binomial")
     for k in ("S", "K", "T", "sigma", "steps"):
-        prog.in_(b[k])
+        prog.in_(t[k])
     prog.out(price).out(gr)
-    prog.args(b["S"], b["K"], b["T"], b["sigma"], b["steps"], b["r"], n, price, gr)
+    prog.args(t["S"], t["K"], t["T"], t["sigma"], t["steps"], r, n, price, gr)
     eng.work_items(n * 32, 32).scheduler("hguided", (2.0, 1.0)).workers(8, 0).program(prog)
     eng.run().synchronize()
     eng.close()
-    assert torch.equal(price, b["price"])
-    assert torch.equal(gr, b["greeks"])
+    return price, gr
+
+
+def test_greeks_pass_bit_exact_across_options_per_warp_and_batching(E):
+    # The greeks pass sets up several options per warp (one per lane: 32 at
+    # 200003 options, 1 at 1037) and sums each option's leaves in turn.  An
+    # option's results must not depend on that grouping, nor on the batched
+    # launch's instance lookup: prices and greeks agree bit for bit,
+    # including options of one step and of the deepest lattice.
+    import torch
+    from paper_1805_02755_gb300.batching import BinomialBatch
+    n, m = 200003, 1037
+    b = make_batches(torch, [n], 830)[0]
+    b["steps"][:3] = 1
+    b["steps"][3:6] = 2048  # the deepest lattice
+    keys = ("S", "K", "T", "sigma", "steps")
+    price, gr = _single_launch(E, torch, {k: b[k] for k in keys}, b["r"])
+    p1, g1 = _single_launch(E, torch, {k: b[k][:m].clone() for k in keys}, b["r"])
+    assert torch.equal(p1, price[:m])
+    assert torch.equal(g1, gr[:m])
+    # the same options as uneven instances of one batched launch
+    sizes, lo, batches = [37, 1, 90000, 2, 109963], 0, []
+    assert sum(sizes) == n
+    for z in sizes:
+        d = {k: b[k][lo:lo + z] for k in keys}
+        d["r"] = b["r"]
+        d["price"] = torch.full((z,), -1.0, device="cuda")
+        d["greeks"] = torch.full((z, 2), -1.0, device="cuda")
+        batches.append(d)
+        lo += z
+    bb = BinomialBatch(batches, with_greeks=True)
+    bb.run()
+    torch.cuda.synchronize()
+    bb.close()
+    assert torch.equal(torch.cat([d["price"] for d in batches]), price)
+    assert torch.equal(torch.cat([d["greeks"] for d in batches]), gr)
 
 
 def test_batches_with_and_without_greeks_arrays_in_one_launch(E, oracle_mod):
