@@ -613,6 +613,8 @@ __device__ __forceinline__ float2 greeks_leaf_sums(const GreeksConsts &k, int N,
     return make_float2(sd * sgn, sv * fv);
 }
 
+// Sums of a pair over the warp (xor butterfly, a fixed order; every lane
+// gets the sums).
 __device__ __forceinline__ float2 warp_sum2(float2 v)
 {
 #pragma unroll
@@ -629,14 +631,6 @@ __device__ __forceinline__ float vega_factor(const Opt &op)
 {
     const float sgn = op.put ? -1.f : 1.f;
     return (op.refl ? -sgn : sgn) * op.S * op.sdt;
-}
-
-// Delta and the vega leaf part of one option from the closed-form adjoint
-// weights, summed over the warp (every lane gets the sums).
-__device__ __forceinline__ float2 closed_form_greeks(const Opt &op, int nz, int lane)
-{
-    const GreeksConsts k = greeks_consts(op);
-    return warp_sum2(greeks_leaf_sums(k, op.N, nz, op.put ? -1.f : 1.f, vega_factor(op), lane));
 }
 
 // The greeks of the banded form in two launches: the lattice kernel leaves
@@ -767,8 +761,9 @@ __global__ void __launch_bounds__(kWarp, FULL ? kMinCtasFull : kMinCtas) k_binom
 // vega from the closed-form sums over the nz nonzero leaves (binomial
 // probabilities, discounted), plus 1 for the calls priced through the put,
 // and the vega term through p that the lattice left in the scratch pair.
-// The batched launch takes the same path, so both agree bit for bit.  The launcher picks per so that the warps still
-// fill the GPU (32 for 2^20 options; 2 for 16384).
+// The batched launch takes the same path, so both agree bit for bit.  The
+// launcher picks per so that the warps still fill the GPU (32 for 2^20
+// options; 2 for 16384).
 constexpr int kGreeksWarps = 8;
 
 // One lane's option in the greeks pass.
