@@ -100,7 +100,7 @@ class Workload:
 
     def make_engine(self, sched, params, D=0, C=0, host=False):
         E = self.E
-        eng = E.Engine(0)
+        eng = E.Engine()
         ins, outs = (self.h_in, self.h_out) if host else (self.d_in, self.d_out)
         eng.work_items(self.gws, self.lws).scheduler(sched, params).workers(D, C)
         eng.program(self.program(ins, outs))
@@ -175,7 +175,7 @@ class Mandelbrot(Workload):
             o = out[row * Wd:(row + h) * Wd]
             y0 = float(np.float32(r["y0"]) + np.float32(row) * np.float32(r["dy"]))
             views.append(dict(out=o, W=Wd, H=h, x0=r["x0"], y0=y0, dx=r["dx"], dy=r["dy"], max_iter=r["max_iter"]))
-            eng = E.Engine(0)
+            eng = E.Engine()
             eng.work_items(-(-(Wd * h) // 4 // 256) * 256, 256).scheduler("static", ()).workers(1, 0)
             eng.program(E.Program("mandelbrot").out(o).args(o, Wd, h, r["x0"], y0, r["dx"], r["dy"], r["max_iter"]))
             engines.append(eng)
@@ -257,7 +257,7 @@ class Gaussian(Workload):
         for h in split_uneven(self.H, 16, seed=13):
             xi, oi = x[row * self.Wd:(row + h) * self.Wd], out[row * self.Wd:(row + h) * self.Wd]
             images.append({"in": xi, "out": oi, "w": w, "W": self.Wd, "H": h})
-            eng = E.Engine(0)
+            eng = E.Engine()
             s, p, D, C = self.sched
             eng.work_items(self.Wd * h, self.lws).scheduler(s, p).workers(D, C)
             if cfg is not None:
@@ -437,7 +437,7 @@ class Binomial(Workload):
 
     def plain_engine(self):
         E = self.E
-        eng = E.Engine(0)
+        eng = E.Engine()
         s, prm, D, C = self.sched
         eng.work_items(self.gws, self.lws).scheduler(s, prm).workers(D, C)
         eng.program(self.program(self.d_in, self.d_out, greeks=False))
@@ -457,7 +457,7 @@ class Binomial(Workload):
                 p.in_(t)
             p.out(price).out(gr)
             p.args(*ins, self.o["r"], hi - lo, price, gr)
-            eng = E.Engine(0)
+            eng = E.Engine()
             eng.work_items((hi - lo) * 32, 32).scheduler(s, prm).workers(D, C).program(p)
             engs.append(eng)
         return engs
@@ -478,7 +478,7 @@ class Binomial(Workload):
             b = dict(S=S[sl], K=K[sl], T=T[sl], sigma=sig[sl], steps=st[sl], r=self.o["r"], price=price[sl],
                       greeks=gr[sl])
             batches.append(b)
-            eng = E.Engine(0)
+            eng = E.Engine()
             p = E.Program("binomial")
             for t in (b["S"], b["K"], b["T"], b["sigma"], b["steps"]):
                 p.in_(t)
@@ -577,7 +577,7 @@ class Gemm(Workload):
         ab = torch.empty(self.A.shape, dtype=torch.bfloat16, device="cuda")
         bb = torch.empty(self.Bt.shape, dtype=torch.bfloat16, device="cuda")
         for src, dst in ((dA, ab), (dB, bb)):  # the input cast, in the library's kernel
-            ce = E.Engine(0)
+            ce = E.Engine()
             pr = E.Program("cast_bf16").in_(src).out(dst).args(src, dst, src.numel())
             ce.work_items(src.numel(), 256).scheduler("dynamic", (256,)).program(pr).run().synchronize()
             ce.close()
@@ -648,7 +648,7 @@ class MultiEngine:
             prog, gws, lws = pr[:3]
             d, c = pr[3] if len(pr) > 3 else (D, C)  # a program may name its own workers
             s, p = pr[4] if len(pr) > 4 and sched != "monolithic" else (sched, params)  # ... and scheduler
-            e = E.Engine(0)
+            e = E.Engine()
             e.work_items(gws, lws).scheduler(s, p).workers(d, c)
             e.program(prog)
             self.engs.append(e)
@@ -1216,7 +1216,7 @@ def fp32_probe(E, torch, sms, sm_mhz, reps=10):
     lws, iters = 256, 512
     G = sms * 8 * 4
     out = torch.empty(G * lws, device="cuda")
-    eng = E.Engine(0)
+    eng = E.Engine()
     eng.work_items(G * lws, lws).scheduler("monolithic", ())
     eng.program(E.Program("fp32_probe").out(out).args(out, iters, 0.999, 0.001))
     s = torch.cuda.current_stream()

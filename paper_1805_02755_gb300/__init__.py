@@ -455,11 +455,21 @@ class Program:
             pass
 
 
-class Engine:
-    """Engine bound to one GPU and one stream (the Tier-1 EngineCL object)."""
+def current_device(device: Optional[int] = None) -> int:
+    """`device`, or torch's current CUDA device when it is None (the GPU this
+    process was given, e.g. LOCAL_RANK's under torchrun)."""
+    if device is not None:
+        return int(device)
+    import torch
+    return torch.cuda.current_device()
 
-    def __init__(self, device: int = 0, stream=None):
-        self.h = ecl_engine_create(device, stream)
+
+class Engine:
+    """Engine bound to one GPU and one stream (the Tier-1 EngineCL object).
+    `device` None: torch's current CUDA device."""
+
+    def __init__(self, device: Optional[int] = None, stream=None):
+        self.h = ecl_engine_create(current_device(device), stream)
         self.program_obj = None
 
     def close(self):

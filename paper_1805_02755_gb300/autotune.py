@@ -14,14 +14,14 @@ from typing import Callable, Dict, List, Optional
 
 import torch
 
-from . import ECL_HGUIDED, Engine, SCHEDULERS, ecl_kernel_occupancy
+from . import ECL_HGUIDED, Engine, SCHEDULERS, current_device, ecl_kernel_occupancy
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ecl_autotune.json")
 
 
-def default_space(kernel: str, G: int, device: int = 0) -> List[Dict]:
+def default_space(kernel: str, G: int, device: Optional[int] = None) -> List[Dict]:
     """Candidate configurations for a program of G work-groups."""
-    sms, per_sm = ecl_kernel_occupancy(kernel, device)
+    sms, per_sm = ecl_kernel_occupancy(kernel, current_device(device))
     resident = sms * max(1, per_sm)
     space = []
     for D in sorted({1, 4, 8, 12, 16, 24, 64, resident}):
@@ -57,7 +57,8 @@ def _time(engine: Engine, reps: int, warmup: int) -> float:
 
 def autotune(kernel: str, make_program: Callable[[], object], gws: int, lws: int,
              space: Optional[List[Dict]] = None, reps: int = 3, warmup: int = 1,
-             cache_path: Optional[str] = DEFAULT_CACHE, device: int = 0, refresh: bool = False) -> Dict:
+             cache_path: Optional[str] = DEFAULT_CACHE, device: Optional[int] = None,
+             refresh: bool = False) -> Dict:
     """Returns {'config': best, 'ms': time, 'table': [(config, ms), ...]}.
 
     ``make_program()`` builds a fresh Program for each candidate (an engine

@@ -26,7 +26,7 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 import torch
 
-from . import Engine, Program
+from . import Engine, Program, current_device
 
 VIEW_DTYPE = np.dtype([("out", "<u8"), ("W", "<i4"), ("H", "<i4"), ("x0", "<f4"), ("y0", "<f4"), ("dx", "<f4"),
                        ("dy", "<f4"), ("max_iter", "<i4"), ("pad", "<i4"), ("first", "<i8"), ("wgs", "<i8")])
@@ -53,7 +53,7 @@ class BinomialBatch:
     and a float r.
     """
 
-    def __init__(self, batches: Sequence[Dict], with_greeks: bool = True, device: int = 0,
+    def __init__(self, batches: Sequence[Dict], with_greeks: bool = True, device: Optional[int] = None,
                  scheduler=("hguided", (2.0, 1.0)), workers=(8, 0), stream=None, config: Optional[Dict] = None):
         self.batches = list(batches)
         tab = np.zeros(len(self.batches), dtype=INSTANCE_DTYPE)
@@ -64,6 +64,7 @@ class BinomialBatch:
                       _ptr(b["price"]), _ptr(b.get("greeks")), first, n, float(b["r"]), 0)
             first += n
         self.total = first
+        device = current_device(device)
         self.table = torch.from_numpy(tab.view(np.uint8).copy()).to(f"cuda:{device}")
         self.engine = Engine(device, stream)
         self.program = Program("binomial_batch").in_(self.table).args(self.table, len(self.batches), self.total,
@@ -99,8 +100,10 @@ class _TableBatch:
     kernel = ""
     lws = 256
 
-    def _finish(self, tab: np.ndarray, total: int, device: int, scheduler, workers, stream, config) -> None:
+    def _finish(self, tab: np.ndarray, total: int, device: Optional[int], scheduler, workers, stream,
+                config) -> None:
         self.total = total
+        device = current_device(device)
         self.table = torch.from_numpy(tab.view(np.uint8).copy()).to(f"cuda:{device}")
         self.engine = Engine(device, stream)
         self.program = Program(self.kernel).in_(self.table).args(self.table, len(tab), total)
@@ -138,8 +141,8 @@ class MandelbrotBatch(_TableBatch):
     def workgroups(W: int, H: int) -> int:
         return -(-(W * H) // (4 * 256))
 
-    def __init__(self, views: Sequence[Dict], device: int = 0, scheduler=("hguided", (2.0, 1.0)), workers=(0, 0),
-                 stream=None, config: Optional[Dict] = None):
+    def __init__(self, views: Sequence[Dict], device: Optional[int] = None, scheduler=("hguided", (2.0, 1.0)),
+                 workers=(0, 0), stream=None, config: Optional[Dict] = None):
         self.views = list(views)
         tab = np.zeros(len(self.views), dtype=VIEW_DTYPE)
         first = 0
@@ -174,8 +177,8 @@ class GaussianBatch(_TableBatch):
     def tiles(W: int, H: int) -> int:
         return -(-H // 32) * -(-W // 224)
 
-    def __init__(self, images: Sequence[Dict], device: int = 0, scheduler=("hguided", (2.0, 1.0)), workers=(0, 0),
-                 stream=None, config: Optional[Dict] = None):
+    def __init__(self, images: Sequence[Dict], device: Optional[int] = None, scheduler=("hguided", (2.0, 1.0)),
+                 workers=(0, 0), stream=None, config: Optional[Dict] = None):
         self.images = list(images)
         tab = np.zeros(len(self.images), dtype=IMAGE_DTYPE)
         first = 0

@@ -117,3 +117,20 @@ def test_job_rate_counts_every_rank():
     import bench
     assert bench.job_rate(1000, 4, 2.0) == 2000.0
     assert bench.max_over_ranks(1.5, 1) == 1.5
+
+
+def test_engines_default_to_torchs_current_device(monkeypatch):
+    # Under torchrun each rank sets its own CUDA device; an engine (and the
+    # batching helpers built on it) created without a device ordinal must
+    # take that device, not device 0.  Checked on the host with the C call
+    # and torch's device query replaced.
+    import torch
+    import paper_1805_02755_gb300 as E
+    seen = []
+    monkeypatch.setattr(E, "ecl_engine_create", lambda device, stream=None: seen.append(device) or 0)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 3)
+    assert E.current_device() == 3
+    assert E.current_device(1) == 1
+    E.Engine()
+    E.Engine(2)
+    assert seen == [3, 2]
